@@ -1,0 +1,191 @@
+/*
+ * bfhe.h -- C ABI of the GB300 library for bridged BFV arithmetic.
+ *
+ * The paper (Chielle, Mazonka, Gamil, Maniatakos, "Accelerating Fully
+ * Homomorphic Encryption by Bridging Modular and Bit-Level Arithmetic",
+ * ICCAD'22) mixes two secure types on one BFV key set (Sec. 3.2): SecureMod,
+ * a native ciphertext mod t, and SecureUint/SecureBool, arrays of ciphertexts
+ * that each encrypt a bit.  This library computes the ciphertext kernels both
+ * reduce to, on one GPU: the gate equations of Sec. 3.1, the bit -> mod
+ * conversion of Listing 5 and the mod -> bit conversion of Eq. 2 / Listings
+ * 7-8, over an RNS BFV (Fan-Vercauteren) evaluator.
+ *
+ * Conventions (every function below):
+ *  - All ciphertext, plaintext and slot buffers are caller-owned DEVICE
+ *    memory on the context's device.  A ciphertext is uint64 [2][L][N]: two
+ *    polynomials, each L RNS limbs of N coefficients, coefficient form,
+ *    residues canonical in [0, q_i).  A batch of n ciphertexts is n of those
+ *    back to back ([n][2][L][N]).  Slot vectors are uint64 [n][N], values < t.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue work and return without synchronising; outputs
+ *    are ready when the stream reaches that point.
+ *  - The context owns keys, tables and a scratch arena (device memory it
+ *    allocates itself with cudaMalloc, grown on demand; growth synchronises
+ *    the device, so reserve with bfhe_reserve before capturing a CUDA graph).
+ *  - Return value: BFHE_OK (0) or a negative BFHE_E* code; no call aborts,
+ *    traps or throws.  Inputs are not checked for canonical residues (cost);
+ *    shapes, parameters and pointers are.
+ *  - Outputs may alias inputs only where stated.
+ *  - Deterministic: the same seeds and inputs give bit-identical outputs.
+ */
+#ifndef BFHE_H
+#define BFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BFHE_OK 0
+#define BFHE_EINVAL (-1)   /* bad shape, size, parameter or NULL pointer   */
+#define BFHE_ENOMEM (-2)   /* device allocation failed                     */
+#define BFHE_ECUDA (-3)    /* a CUDA call failed (see bfhe_last_cuda_error) */
+#define BFHE_ETIMEOUT (-4) /* a device-side wait gave up                   */
+#define BFHE_ESTATE (-5)   /* call out of order (e.g. encrypt before keygen) */
+
+typedef struct bfhe_ctx bfhe_ctx;
+
+/* Parameters.  The moduli follow one rule (the paper fixes only n, t and the
+ * security level and lets SEAL pick the rest, Sec. 4.1): every modulus is a
+ * prime q = 1 (mod 2N) below 2^prime_bits taken from one downward scan over
+ * q = 2N k + 1 skipping t; the first L are the data primes (Q), the next
+ * alpha the special primes of relinearisation (P), the next K the auxiliary
+ * base of the exact multiply, K being the least count with B > 2 t N Q. */
+typedef struct {
+    uint32_t N;          /* ring degree, power of two, 1024 .. 32768          */
+    uint32_t L;          /* data primes, 1 .. 16                               */
+    uint32_t alpha;      /* special primes, 1 or 2                             */
+    uint32_t prime_bits; /* bit size of every modulus, 30 .. 60 (default 50)   */
+    uint64_t t;          /* plaintext modulus: a prime = 1 (mod 2N), < 2^32    */
+} bfhe_params;
+
+/* Create a context on CUDA device `device`.  Builds the moduli, NTT twiddles
+ * and RNS constants on the host and uploads them.  *out is set on success. */
+int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** out);
+void bfhe_ctx_destroy(bfhe_ctx* ctx);
+
+/* Moduli in library order: primes_out[0 .. L+alpha+K-1] = q_0..q_{L-1},
+ * p_0..p_{alpha-1}, b_0..b_{K-1} (host buffer of at least 64 entries);
+ * *K_out = K.  Also usable before keygen. */
+int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out);
+
+/* Reserve scratch for batches of up to n ciphertexts in every call (avoids
+ * growth, hence device synchronisation, inside later calls). */
+int bfhe_reserve(bfhe_ctx* ctx, size_t n);
+
+/* Key generation from `seed` (keys stay resident on the device): secret s
+ * ternary, pk = ([-(a s + e)]_Q, a), relinearisation keys for the RNS digits
+ * j = 0..L-1: ([-(a_j s + e_j) + P g_j s^2]_{PQ}, a_j), g_j = (Q/q_j)
+ * [(Q/q_j)^-1]_{q_j}; randomness from Philox4x64-10 keyed by (seed, purpose).
+ * Same key set for SecureMod and bit-level types (Sec. 3.2). */
+int bfhe_keygen(bfhe_ctx* ctx, uint64_t seed, void* stream);
+
+/* Copy keys out (device buffers), in coefficient form:
+ *   sk : int64 [N] in {-1, 0, 1}
+ *   pk : uint64 [2][L][N]
+ *   rlk: uint64 [L][2][L+alpha][N]  (digit j, component (b_j, a_j), limbs
+ *        over q_0..q_{L-1}, p_0..p_{alpha-1})
+ * Any pointer may be NULL to skip that key. */
+int bfhe_export_keys(bfhe_ctx* ctx, int64_t* sk, uint64_t* pk, uint64_t* rlk, void* stream);
+
+/* Encrypt n slot vectors (slots uint64 [n][N], each < t) into ct_out
+ * [n][2][L][N]: (Delta m + pk0 u + e1, pk1 u + e2) mod Q with m the batch
+ * encoding (slot j = m(zeta^(2j+1)) mod t, Sec. 2.3) and u, e1, e2 drawn
+ * from Philox4x64-10 with key (seed, purpose) and poly index = batch index. */
+int bfhe_encrypt(bfhe_ctx* ctx, const uint64_t* slots, size_t n, uint64_t seed,
+                 uint64_t* ct_out, void* stream);
+
+/* Decrypt n ciphertexts into slots uint64 [n][N]: m = [round(t [c0 + c1 s]_Q
+ * / Q)]_t computed exactly, then decoded. */
+int bfhe_decrypt(bfhe_ctx* ctx, const uint64_t* ct, size_t n, uint64_t* slots_out, void* stream);
+
+/* Linear operations (Sec. 3.1 uses them in every gate; Listing 5 is only
+ * additions).  out may alias a or b.  A public constant c (< t) enters as
+ * the trivial ciphertext (Delta c, 0). */
+int bfhe_add(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n, void* stream);
+int bfhe_sub(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n, void* stream);
+int bfhe_add_const(bfhe_ctx* ctx, const uint64_t* a, uint64_t c, uint64_t* out, size_t n, void* stream);
+int bfhe_sub_const(bfhe_ctx* ctx, const uint64_t* a, uint64_t c, uint64_t* out, size_t n, void* stream);
+int bfhe_const_sub(bfhe_ctx* ctx, uint64_t c, const uint64_t* a, uint64_t* out, size_t n, void* stream);
+/* Multiply both components by the integer c (< t). */
+int bfhe_mul_scalar(bfhe_ctx* ctx, const uint64_t* a, uint64_t c, uint64_t* out, size_t n, void* stream);
+/* Slot-wise product with public vectors: plain uint64 [n][N] slot values
+ * (< t), encoded to [0, t)^N coefficients; out = (c0 pt, c1 pt) mod Q. */
+int bfhe_mul_plain(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* plain, uint64_t* out, size_t n,
+                   void* stream);
+
+/* Ciphertext product with relinearisation, exact FV: lift inputs to the
+ * centred range, tensor over Z (computed in RNS over Q and the auxiliary
+ * base), round(t d / Q) mod Q, then key switching of d2 with the digit
+ * gadget and rounding division by P.  out must not alias a or b.
+ * a[i] * b[i] for i < n. */
+int bfhe_mul_relin(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n,
+                   void* stream);
+
+/* Homomorphic gates over encrypted bits (Sec. 3.1): AND = xy,
+ * NAND = 1 - xy, OR = x + y - xy, NOR = 1 - OR, XOR = x + y - 2xy,
+ * XNOR = 1 - XOR, NOT = 1 - x, MUX(x, y, z) = x (y - z) + z.
+ * y is ignored for NOT; z is used by MUX only.  One multiply per gate
+ * (none for NOT).  out must not alias the inputs. */
+enum { BFHE_AND = 0, BFHE_OR = 1, BFHE_XOR = 2, BFHE_NAND = 3, BFHE_NOR = 4, BFHE_XNOR = 5,
+       BFHE_NOT = 6, BFHE_MUX = 7 };
+int bfhe_bit_gate(bfhe_ctx* ctx, int gate, const uint64_t* x, const uint64_t* y, const uint64_t* z,
+                  uint64_t* out, size_t n, void* stream);
+
+/* A levelised gate list over one wire array: all gates of one circuit depth
+ * level share one batched multiply.  wires: uint64 [n_wires][n][2][L][N]
+ * (n slot-packed ciphertexts per wire); table: DEVICE int32 [n_gates][5] =
+ * (gate, x, y, z, out) wire indices (unused inputs ignored), the n_mul gates
+ * with a multiply first and the NOT gates after them.  No gate may read a
+ * wire that another gate of the same call writes.  Counts only the
+ * multiplies (the table stays on the device).  Capturable in a CUDA graph
+ * once scratch is reserved. */
+int bfhe_gate_level(bfhe_ctx* ctx, uint64_t* wires, size_t n_wires, size_t n, const int32_t* table,
+                    size_t n_gates, size_t n_mul, void* stream);
+
+/* SecureUint<s> -> SecureMod (Sec. 3.2.1, Listing 5): Horner's scheme
+ * r = v[s-1]; r += r + v[i] for i = s-2 .. 0, i.e. sum_i 2^i v[i] mod Q.
+ * bits: uint64 [s][n][2][L][N] (bit 0 first); out [n][2][L][N].
+ * 2(s-1) additions, no multiplies. */
+int bfhe_bits_to_mod(bfhe_ctx* ctx, const uint64_t* bits, uint32_t s, uint64_t* out, size_t n,
+                     void* stream);
+
+/* SecureMod -> SecureUint<s> (Sec. 3.2.3, Eq. 2, Listings 7-8): for every
+ * candidate c in [c_lo, c_hi], eq_c = 1 - (x - c)^(t-1) by the square-and-
+ * multiply recursion of Listing 7; then
+ *   mode BFHE_PAPER : bit k += AND(trivial(bit k of c), eq_c)  (s multiplies
+ *                     per candidate: the count the paper states),
+ *   mode BFHE_SELECT: bit k += eq_c where bit k of c is 1 (no multiply).
+ * x: [n][2][L][N]; bits_out: [s][n][2][L][N].  Chains of all candidates run
+ * batched. */
+enum { BFHE_PAPER = 0, BFHE_SELECT = 1 };
+int bfhe_mod_to_bits(bfhe_ctx* ctx, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
+                     uint64_t* bits_out, size_t n, void* stream);
+
+/* Power by the recursion of Listing 7 (floor(log2 e) + w(e) - 1 multiplies):
+ * out[i] = x[i]^e, e >= 1.  out must not alias x. */
+int bfhe_pow(bfhe_ctx* ctx, const uint64_t* x, uint64_t e, uint64_t* out, size_t n, void* stream);
+
+/* Operation counters kept with the paper's accounting (Table 1 counts
+ * ciphertext add / mul / sub): out[0] = additions, out[1] = subtractions,
+ * out[2] = ciphertext multiplies, out[3] = plaintext multiplies.  Reset
+ * when reset != 0 (after reading). */
+int bfhe_op_counts(bfhe_ctx* ctx, uint64_t out[4], int reset);
+
+/* Negacyclic NTT of a batch of polynomials in place, for tests and tools:
+ * data uint64 [n_polys][n_limbs][N] over the first n_limbs data primes
+ * (n_limbs <= L); forward maps coefficients to the library's internal
+ * evaluation order, inverse maps back (inputs canonical). */
+int bfhe_ntt(bfhe_ctx* ctx, uint64_t* data, size_t n_polys, uint32_t n_limbs, int inverse, void* stream);
+
+/* Message of the last failed call on this thread (static storage). */
+const char* bfhe_strerror(int code);
+const char* bfhe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFHE_H */

@@ -1,0 +1,537 @@
+// api.cu -- the C ABI (include/bfhe.h): validation, scratch layout and kernel sequencing.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace {
+
+// Philox purposes (key word 1)
+enum : u64 { P_SK = 1, P_PK_A = 2, P_PK_E = 3, P_RLK_A = 4, P_RLK_E = 5, P_ENC_U = 6, P_ENC_E1 = 7, P_ENC_E2 = 8 };
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+// device-memory budget for one call's scratch (batches beyond it are tiled)
+size_t g_scratch_budget = (size_t)16 << 30;
+
+#define CHECK_CTX(ctx)                                                     \
+    do {                                                                   \
+        if (!(ctx)) return set_error(BFHE_EINVAL, "null context");         \
+    } while (0)
+#define CHECK_KEYS(ctx)                                                    \
+    do {                                                                   \
+        if (!(ctx)->have_keys) return set_error(BFHE_ESTATE, "no keys: call bfhe_keygen first"); \
+    } while (0)
+#define RC(x)                                \
+    do {                                     \
+        int _rc = (x);                       \
+        if (_rc != BFHE_OK) return _rc;      \
+    } while (0)
+
+size_t mul_words_per_ct(const bfhe_ctx* c) { return mul_scratch_bytes(c, 1) / sizeof(u64); }
+
+// largest tile of ciphertexts whose multiply scratch fits in `bytes`
+size_t mul_tile(const bfhe_ctx* c, size_t bytes) {
+    size_t per = mul_scratch_bytes(c, 1);
+    size_t t = bytes / per;
+    return t ? t : 1;
+}
+
+// out[i] = a[i] * b[i] (relinearised), n ciphertexts, scratch of `scratch_words` words
+int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, u64* scratch,
+                   size_t scratch_words, cudaStream_t st) {
+    const size_t N = c->N, L = c->L, K = c->K, LK = L + K, QP = L + c->alpha;
+    const size_t per = mul_words_per_ct(c);
+    size_t tile = scratch_words / per;
+    if (tile == 0) return set_error(BFHE_ENOMEM, "scratch too small for one multiply");
+    const size_t ctw = c->ct_words();
+    for (size_t c0 = 0; c0 < n; c0 += tile) {
+        const int m = (int)std::min(tile, n - c0);
+        u64* X = scratch;                                  // [m][4][LK][N]
+        u64* C3 = X + (size_t)m * 4 * LK * N;              // [m][3][L][N]
+        u64* Dg = C3 + (size_t)m * 3 * L * N;              // [m][L][QP][N]
+        u64* W = Dg + (size_t)m * L * QP * N;              // [m][2][QP][N]
+        const u64* a = A + c0 * ctw;
+        const u64* b = B + c0 * ctw;
+        u64* o = out + c0 * ctw;
+        RC(launch_modup(c, a, b, X, m, st));
+        RC(launch_ntt_fwd(c, ntt_io(X, X, LK, N), 4 * m, (int)LK, c->mapQB(), st));
+        RC(launch_tensor(c, X, m, st));
+        NttIO io3;
+        io3.in = X;
+        io3.out = X;
+        io3.n_inner = 3;
+        io3.in_os = io3.out_os = 4 * LK * N;
+        io3.in_is = io3.out_is = LK * N;
+        io3.in_ls = io3.out_ls = N;
+        RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st));
+        RC(launch_scale(c, X, C3, m, st));
+        NttIO iod;   // digit j of c2 (limb j of C3 slot 2), reduced into every prime of Q u P
+        iod.in = C3 + 2 * L * N;
+        iod.out = Dg;
+        iod.n_inner = (int)L;
+        iod.in_os = 3 * L * N;
+        iod.in_is = N;
+        iod.in_ls = 0;
+        iod.out_os = L * QP * N;
+        iod.out_is = QP * N;
+        iod.out_ls = N;
+        RC(launch_ntt_fwd(c, iod, m * (int)L, (int)QP, c->mapQP(), st));
+        RC(launch_inner(c, Dg, W, m, st));
+        RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st));
+        RC(launch_moddown(c, W, C3, o, m, st));
+    }
+    return BFHE_OK;
+}
+
+int scratch_for(bfhe_ctx* c, size_t fixed_words, size_t n_mul, u64** fixed, u64** mul, size_t* mul_words) {
+    const size_t per = mul_words_per_ct(c);
+    size_t budget_words = g_scratch_budget / sizeof(u64);
+    size_t want_mul = n_mul * per;
+    if (fixed_words + want_mul > budget_words) {
+        const size_t room = budget_words > fixed_words ? budget_words - fixed_words : 0;
+        want_mul = std::max(per, (room / per) * per);
+    }
+    if (n_mul == 0) want_mul = 0;
+    void* p;
+    RC(ctx_scratch(c, (fixed_words + want_mul) * sizeof(u64), &p));
+    *fixed = (u64*)p;
+    *mul = (u64*)p + fixed_words;
+    *mul_words = want_mul;
+    return BFHE_OK;
+}
+
+int pow_impl(bfhe_ctx* c, const u64* x, u64 e, u64* out, size_t n, u64* bufs, u64* mul, size_t mul_words,
+             cudaStream_t st) {
+    // Listing 7: pow(b, e) = pow(b*b, e >> 1) [* b if e odd]; unrolled: squarings b^(2^d) for
+    // d = 1..top, then the odd-bit factors multiplied in from the deepest level up.
+    const size_t ctw = c->ct_words();
+    int top = 63 - __builtin_clzll(e);
+    // bufs: [2][n] ping-pong for the squaring chain, then one slot per set bit below top
+    u64* cur = bufs;
+    u64* nxt = bufs + n * ctw;
+    u64* saved = bufs + 2 * n * ctw;
+    std::vector<std::pair<int, u64*>> keep;
+    int nkeep = 0;
+    const u64* base = x;
+    if ((e & 1) && top > 0) {
+        keep.push_back({0, (u64*)x});
+    }
+    for (int d = 1; d <= top; ++d) {
+        RC(mul_relin_impl(c, base, base, nxt, n, mul, mul_words, st));
+        c->counts[2] += n;
+        std::swap(cur, nxt);
+        base = cur;
+        if (d < top && ((e >> d) & 1)) {
+            u64* slot = saved + (size_t)nkeep * n * ctw;
+            BFHE_CUDA(cudaMemcpyAsync(slot, cur, n * ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+            keep.push_back({d, slot});
+            ++nkeep;
+        }
+    }
+    // r = b^(2^top); then r *= b^(2^d) for set bits d < top, deepest first
+    const u64* r = base;
+    for (int k = (int)keep.size() - 1; k >= 0; --k) {
+        u64* dst = (r == cur) ? nxt : cur;
+        RC(mul_relin_impl(c, r, keep[k].second, dst, n, mul, mul_words, st));
+        c->counts[2] += n;
+        r = dst;
+    }
+    if (r != out) BFHE_CUDA(cudaMemcpyAsync(out, r, n * ctw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    return BFHE_OK;
+}
+
+size_t pow_buf_words(const bfhe_ctx* c, u64 e, size_t n) {
+    int pc = __builtin_popcountll(e);
+    return (size_t)(2 + pc) * n * c->ct_words();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" int bfhe_reserve(bfhe_ctx* c, size_t n) {
+    CHECK_CTX(c);
+    void* p;
+    return ctx_scratch(c, std::min(mul_scratch_bytes(c, n) + 8 * n * c->ct_words() * sizeof(u64), g_scratch_budget), &p);
+}
+
+extern "C" int bfhe_keygen(bfhe_ctx* c, uint64_t seed, void* stream) {
+    CHECK_CTX(c);
+    const size_t N = c->N, L = c->L, QP = c->L + c->alpha;
+    cudaStream_t st = S(stream);
+    BFHE_CUDA(cudaSetDevice(c->device));
+    if (!c->d_sk) {
+        BFHE_CUDA(cudaMalloc(&c->d_sk, N * sizeof(i64)));
+        BFHE_CUDA(cudaMalloc(&c->d_sk_ntt, QP * N * sizeof(u64)));
+        BFHE_CUDA(cudaMalloc(&c->d_pk, 2 * L * N * sizeof(u64)));
+        BFHE_CUDA(cudaMalloc(&c->d_pk_ntt, 2 * L * N * sizeof(u64)));
+        BFHE_CUDA(cudaMalloc(&c->d_rlk_ntt, L * 2 * QP * N * sizeof(u64)));
+    }
+    // scratch: A[L][N], AS[L][N], e[N], S2[QP][N], ASj[L][QP][N], Bj[L][QP][N], ej[L][N]
+    const size_t words = 2 * L * N + N + QP * N + 2 * L * QP * N + L * N;
+    void* p;
+    RC(ctx_scratch(c, words * sizeof(u64), &p));
+    u64* A = (u64*)p;
+    u64* AS = A + L * N;
+    i64* e = (i64*)(AS + L * N);
+    u64* S2 = (u64*)(e + N);
+    u64* ASj = S2 + QP * N;
+    u64* Bj = ASj + L * QP * N;
+    i64* ej = (i64*)(Bj + L * QP * N);
+
+    // secret key, ternary, and its NTT over Q u P
+    RC(launch_sample_small(c, c->d_sk, 1, seed, P_SK, 0, 0, st));
+    RC(launch_spread(c, c->d_sk, c->d_sk_ntt, 1, (int)QP, c->mapQP(), st));
+    RC(launch_ntt_fwd(c, ntt_io(c->d_sk_ntt, c->d_sk_ntt, QP, N), 1, (int)QP, c->mapQP(), st));
+    // pk = (-(a s + e), a)
+    RC(launch_sample_uniform(c, A, 1, (int)L, c->mapQ(), seed, P_PK_A, 0, st));
+    BFHE_CUDA(cudaMemcpyAsync(c->d_pk + L * N, A, L * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    RC(launch_ntt_fwd(c, ntt_io(A, A, L, N), 1, (int)L, c->mapQ(), st));
+    PwStrides s1{0, 0, 0, 0, 0, 0};
+    RC(launch_pointwise(c, A, c->d_sk_ntt, AS, 1, 1, (int)L, c->mapQ(), s1, st));
+    RC(launch_ntt_inv(c, ntt_io(AS, AS, L, N), 1, (int)L, c->mapQ(), 1, st));
+    RC(launch_sample_small(c, e, 1, seed, P_PK_E, 0, 1, st));
+    RC(launch_neg_add_small(c, AS, e, c->d_pk, 1, (int)L, c->mapQ(), nullptr, 0, st));
+    RC(launch_ntt_fwd(c, ntt_io(c->d_pk, c->d_pk_ntt, L, N), 2, (int)L, c->mapQ(), st));
+    // s^2 over Q u P (coefficient form)
+    RC(launch_pointwise(c, c->d_sk_ntt, c->d_sk_ntt, S2, 1, 1, (int)QP, c->mapQP(), s1, st));
+    RC(launch_ntt_inv(c, ntt_io(S2, S2, QP, N), 1, (int)QP, c->mapQP(), 1, st));
+    // relinearisation keys: a_j uniform over Q u P, NTT straight into rlk[j][1]
+    u64* Araw = Bj;   // staging for the raw a_j before NTT
+    RC(launch_sample_uniform(c, Araw, (int)L, (int)QP, c->mapQP(), seed, P_RLK_A, 0, st));
+    NttIO ioa;
+    ioa.in = Araw;
+    ioa.out = c->d_rlk_ntt + QP * N;
+    ioa.n_inner = 1;
+    ioa.in_os = QP * N;
+    ioa.in_is = 0;
+    ioa.in_ls = N;
+    ioa.out_os = 2 * QP * N;
+    ioa.out_is = 0;
+    ioa.out_ls = N;
+    RC(launch_ntt_fwd(c, ioa, (int)L, (int)QP, c->mapQP(), st));
+    PwStrides s2{2 * QP * N, 0, 0, 0, QP * N, 0};
+    RC(launch_pointwise(c, c->d_rlk_ntt + QP * N, c->d_sk_ntt, ASj, (int)L, 1, (int)QP, c->mapQP(), s2, st));
+    RC(launch_ntt_inv(c, ntt_io(ASj, ASj, QP, N), (int)L, (int)QP, c->mapQP(), 1, st));
+    RC(launch_sample_small(c, ej, (int)L, seed, P_RLK_E, 0, 1, st));
+    RC(launch_neg_add_small(c, ASj, ej, Bj, (int)L, (int)QP, c->mapQP(), S2, 1, st));
+    NttIO iob = ioa;
+    iob.in = Bj;
+    iob.out = c->d_rlk_ntt;
+    RC(launch_ntt_fwd(c, iob, (int)L, (int)QP, c->mapQP(), st));
+    c->have_keys = true;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_export_keys(bfhe_ctx* c, int64_t* sk, uint64_t* pk, uint64_t* rlk, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    const size_t N = c->N, L = c->L, QP = c->L + c->alpha;
+    cudaStream_t st = S(stream);
+    if (sk) BFHE_CUDA(cudaMemcpyAsync(sk, c->d_sk, N * sizeof(i64), cudaMemcpyDeviceToDevice, st));
+    if (pk) BFHE_CUDA(cudaMemcpyAsync(pk, c->d_pk, 2 * L * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    if (rlk) RC(launch_ntt_inv(c, ntt_io(c->d_rlk_ntt, rlk, QP, N), (int)(2 * L), (int)QP, c->mapQP(), 0, st));
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_encrypt(bfhe_ctx* c, const uint64_t* slots, size_t n, uint64_t seed, uint64_t* ct_out,
+                            void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!slots || !ct_out) return set_error(BFHE_EINVAL, "null buffer");
+    const size_t N = c->N, L = c->L;
+    cudaStream_t st = S(stream);
+    // scratch: M[n][N], u/e1/e2 [3][n][N], U[n][L][N]
+    void* p;
+    RC(ctx_scratch(c, (4 * n * N + n * L * N) * sizeof(u64), &p));
+    u64* M = (u64*)p;
+    i64* u = (i64*)(M + n * N);
+    i64* e1 = u + n * N;
+    i64* e2 = e1 + n * N;
+    u64* U = (u64*)(e2 + n * N);
+    RC(launch_permute(c, slots, M, (int)n, 1, st));
+    RC(launch_ntt_inv(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), 0, st));
+    RC(launch_sample_small(c, u, (int)n, seed, P_ENC_U, 0, 0, st));
+    RC(launch_sample_small(c, e1, (int)n, seed, P_ENC_E1, 0, 1, st));
+    RC(launch_sample_small(c, e2, (int)n, seed, P_ENC_E2, 0, 1, st));
+    RC(launch_spread(c, u, U, (int)n, (int)L, c->mapQ(), st));
+    RC(launch_ntt_fwd(c, ntt_io(U, U, L, N), (int)n, (int)L, c->mapQ(), st));
+    PwStrides s{L * N, 0, 0, L * N, 2 * L * N, L * N};
+    RC(launch_pointwise(c, U, c->d_pk_ntt, ct_out, (int)n, 2, (int)L, c->mapQ(), s, st));
+    RC(launch_ntt_inv(c, ntt_io(ct_out, ct_out, L, N), (int)(2 * n), (int)L, c->mapQ(), 1, st));
+    RC(launch_enc_finish(c, ct_out, M, e1, e2, (int)n, st));
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_decrypt(bfhe_ctx* c, const uint64_t* ct, size_t n, uint64_t* slots_out, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!ct || !slots_out) return set_error(BFHE_EINVAL, "null buffer");
+    const size_t N = c->N, L = c->L;
+    cudaStream_t st = S(stream);
+    void* p;
+    RC(ctx_scratch(c, (n * L * N + n * N) * sizeof(u64), &p));
+    u64* V = (u64*)p;
+    u64* M = V + n * L * N;
+    NttIO io;
+    io.in = ct + L * N;
+    io.out = V;
+    io.n_inner = 1;
+    io.in_os = 2 * L * N;
+    io.in_is = 0;
+    io.in_ls = N;
+    io.out_os = L * N;
+    io.out_is = 0;
+    io.out_ls = N;
+    RC(launch_ntt_fwd(c, io, (int)n, (int)L, c->mapQ(), st));
+    PwStrides s{L * N, 0, 0, 0, L * N, 0};
+    RC(launch_pointwise(c, V, c->d_sk_ntt, V, (int)n, 1, (int)L, c->mapQ(), s, st));
+    RC(launch_ntt_inv(c, ntt_io(V, V, L, N), (int)n, (int)L, c->mapQ(), 1, st));
+    RC(launch_dec_finish(c, V, ct, M, (int)n, st));
+    RC(launch_ntt_fwd(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), st));
+    RC(launch_permute(c, M, slots_out, (int)n, 0, st));
+    return BFHE_OK;
+}
+
+static int lin(bfhe_ctx* c, u64* out, const u64* x, const u64* y, LinCoef cf, u64 cval, size_t n, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return BFHE_OK;
+    if (!out || (cf.cx && !x) || (cf.cy && !y)) return set_error(BFHE_EINVAL, "null buffer");
+    if (cval >= c->t) return set_error(BFHE_EINVAL, "constant must be < t");
+    return launch_lincomb(c, out, x, y, nullptr, nullptr, cf, cval, n, S(stream));
+}
+
+extern "C" int bfhe_add(bfhe_ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n, void* st) {
+    RC(lin(c, out, a, b, LinCoef{0, 1, 1, 0, 0}, 0, n, st));
+    c->counts[0] += n;
+    return BFHE_OK;
+}
+extern "C" int bfhe_sub(bfhe_ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n, void* st) {
+    RC(lin(c, out, a, b, LinCoef{0, 1, -1, 0, 0}, 0, n, st));
+    c->counts[1] += n;
+    return BFHE_OK;
+}
+extern "C" int bfhe_add_const(bfhe_ctx* c, const uint64_t* a, uint64_t k, uint64_t* out, size_t n, void* st) {
+    RC(lin(c, out, a, nullptr, LinCoef{1, 1, 0, 0, 0}, k, n, st));
+    c->counts[0] += n;
+    return BFHE_OK;
+}
+extern "C" int bfhe_sub_const(bfhe_ctx* c, const uint64_t* a, uint64_t k, uint64_t* out, size_t n, void* st) {
+    RC(lin(c, out, a, nullptr, LinCoef{-1, 1, 0, 0, 0}, k, n, st));
+    c->counts[1] += n;
+    return BFHE_OK;
+}
+extern "C" int bfhe_const_sub(bfhe_ctx* c, uint64_t k, const uint64_t* a, uint64_t* out, size_t n, void* st) {
+    RC(lin(c, out, a, nullptr, LinCoef{1, -1, 0, 0, 0}, k, n, st));
+    c->counts[1] += n;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_mul_scalar(bfhe_ctx* c, const uint64_t* a, uint64_t k, uint64_t* out, size_t n, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return BFHE_OK;
+    if (!a || !out) return set_error(BFHE_EINVAL, "null buffer");
+    if (k >= c->t) return set_error(BFHE_EINVAL, "scalar must be < t");
+    RC(launch_mul_scalar(c, a, k, out, n, S(stream)));
+    c->counts[3] += n;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_mul_plain(bfhe_ctx* c, const uint64_t* a, const uint64_t* plain, uint64_t* out, size_t n,
+                              void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return BFHE_OK;
+    if (!a || !plain || !out) return set_error(BFHE_EINVAL, "null buffer");
+    const size_t N = c->N, L = c->L;
+    cudaStream_t st = S(stream);
+    void* p;
+    RC(ctx_scratch(c, (n * N + n * L * N + 2 * n * L * N) * sizeof(u64), &p));
+    u64* M = (u64*)p;
+    u64* PT = M + n * N;
+    u64* CT = PT + n * L * N;
+    RC(launch_permute(c, plain, M, (int)n, 1, st));
+    RC(launch_ntt_inv(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), 0, st));
+    RC(launch_spread(c, (const i64*)M, PT, (int)n, (int)L, c->mapQ(), st));
+    RC(launch_ntt_fwd(c, ntt_io(PT, PT, L, N), (int)n, (int)L, c->mapQ(), st));
+    RC(launch_ntt_fwd(c, ntt_io(a, CT, L, N), (int)(2 * n), (int)L, c->mapQ(), st));
+    PwStrides s{2 * L * N, L * N, L * N, 0, 2 * L * N, L * N};
+    RC(launch_pointwise(c, CT, PT, out, (int)n, 2, (int)L, c->mapQ(), s, st));
+    RC(launch_ntt_inv(c, ntt_io(out, out, L, N), (int)(2 * n), (int)L, c->mapQ(), 1, st));
+    c->counts[3] += n;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_mul_relin(bfhe_ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n,
+                              void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!a || !b || !out) return set_error(BFHE_EINVAL, "null buffer");
+    if (out == a || out == b) return set_error(BFHE_EINVAL, "out must not alias an input");
+    u64 *fixed, *mul;
+    size_t mw;
+    RC(scratch_for(c, 0, n, &fixed, &mul, &mw));
+    RC(mul_relin_impl(c, a, b, out, n, mul, mw, S(stream)));
+    c->counts[2] += n;
+    return BFHE_OK;
+}
+
+static const LinCoef kGate[8] = {
+    {0, 0, 0, 0, 1}, {0, 1, 1, 0, -1}, {0, 1, 1, 0, -2}, {1, 0, 0, 0, -1},
+    {1, -1, -1, 0, 1}, {1, -1, -1, 0, 2}, {1, -1, 0, 0, 0}, {0, 0, 0, 1, 1},
+};
+// (add, sub) per gate with the gate equations written as in Sec. 3.1
+static const int kGateAddSub[8][2] = {{0, 0}, {1, 1}, {2, 1}, {0, 1}, {1, 2}, {2, 2}, {0, 1}, {1, 1}};
+
+extern "C" int bfhe_bit_gate(bfhe_ctx* c, int gate, const uint64_t* x, const uint64_t* y, const uint64_t* z,
+                             uint64_t* out, size_t n, void* stream) {
+    CHECK_CTX(c);
+    if (gate < 0 || gate > 7) return set_error(BFHE_EINVAL, "unknown gate");
+    if (n == 0) return BFHE_OK;
+    if (!x || !out || (gate != BFHE_NOT && !y) || (gate == BFHE_MUX && !z))
+        return set_error(BFHE_EINVAL, "null buffer");
+    cudaStream_t st = S(stream);
+    const size_t ctw = c->ct_words();
+    if (gate == BFHE_NOT) {
+        RC(launch_lincomb(c, out, x, nullptr, nullptr, nullptr, kGate[gate], 1, n, st));
+    } else {
+        CHECK_KEYS(c);
+        if (out == x || out == y || out == z) return set_error(BFHE_EINVAL, "out must not alias an input");
+        u64 *fixed, *mul;
+        size_t mw;
+        const bool mux = gate == BFHE_MUX;
+        RC(scratch_for(c, (mux ? 2 : 1) * n * ctw, n, &fixed, &mul, &mw));
+        u64* P = fixed;
+        const u64* rhs = y;
+        if (mux) {
+            u64* D = fixed + n * ctw;
+            RC(launch_lincomb(c, D, y, z, nullptr, nullptr, LinCoef{0, 1, -1, 0, 0}, 0, n, st));
+            rhs = D;
+        }
+        RC(mul_relin_impl(c, x, rhs, P, n, mul, mw, st));
+        RC(launch_lincomb(c, out, x, y, z, P, kGate[gate], 1, n, st));
+        c->counts[2] += n;
+    }
+    c->counts[0] += n * kGateAddSub[gate][0];
+    c->counts[1] += n * kGateAddSub[gate][1];
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_gate_level(bfhe_ctx* c, uint64_t* wires, size_t n_wires, size_t n, const int32_t* table,
+                               size_t n_gates, size_t n_mul, void* stream) {
+    CHECK_CTX(c);
+    if (n == 0 || n_gates == 0) return BFHE_OK;
+    if (!wires || !table || n_mul > n_gates || n_wires == 0) return set_error(BFHE_EINVAL, "bad gate level");
+    cudaStream_t st = S(stream);
+    const size_t ctw = n * c->ct_words();
+    if (n_mul) {
+        CHECK_KEYS(c);
+        u64 *fixed, *mul;
+        size_t mw;
+        RC(scratch_for(c, 3 * n_mul * ctw, n_mul * n, &fixed, &mul, &mw));
+        u64* AB = fixed;
+        u64* P = fixed + 2 * n_mul * ctw;
+        RC(launch_gather(c, AB, wires, n, table, (int)n_mul, 0, 0, st));
+        RC(mul_relin_impl(c, AB, AB + n_mul * ctw, P, n_mul * n, mul, mw, st));
+        RC(launch_gate_epilogue(c, wires, n, table, (int)n_gates, P, (int)n_mul, st));
+        c->counts[2] += n_mul * n;
+    } else {
+        RC(launch_gate_epilogue(c, wires, n, table, (int)n_gates, nullptr, 0, st));
+    }
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_bits_to_mod(bfhe_ctx* c, const uint64_t* bits, uint32_t s, uint64_t* out, size_t n,
+                                void* stream) {
+    CHECK_CTX(c);
+    if (n == 0) return BFHE_OK;
+    if (!bits || !out || s == 0) return set_error(BFHE_EINVAL, "bad arguments");
+    RC(launch_horner(c, bits, s, out, n, S(stream)));
+    c->counts[0] += (uint64_t)2 * (s - 1) * n;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_pow(bfhe_ctx* c, const uint64_t* x, uint64_t e, uint64_t* out, size_t n, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!x || !out || e == 0) return set_error(BFHE_EINVAL, "bad arguments");
+    if (out == x) return set_error(BFHE_EINVAL, "out must not alias x");
+    cudaStream_t st = S(stream);
+    if (e == 1) {
+        BFHE_CUDA(cudaMemcpyAsync(out, x, n * c->ct_words() * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+        return BFHE_OK;
+    }
+    u64 *fixed, *mul;
+    size_t mw;
+    RC(scratch_for(c, pow_buf_words(c, e, n), n, &fixed, &mul, &mw));
+    return pow_impl(c, x, e, out, n, fixed, mul, mw, st);
+}
+
+extern "C" int bfhe_mod_to_bits(bfhe_ctx* c, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
+                                uint64_t* bits_out, size_t n, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!x || !bits_out || s == 0 || s > 63 || c_hi < c_lo || c_hi >= c->t || (mode != BFHE_PAPER && mode != BFHE_SELECT))
+        return set_error(BFHE_EINVAL, "bad arguments");
+    cudaStream_t st = S(stream);
+    const size_t ctw = c->ct_words();
+    const u64 e = c->t - 1;
+    const size_t total = c_hi - c_lo + 1;
+    // candidates per tile: chain buffers (2 + popcount(e)) + PAPER's trivial bits, eq copies and products (3s)
+    const size_t per_cand = n * ctw * (pow_buf_words(c, e, 1) / ctw + (mode == BFHE_PAPER ? 3 * s : 0) + 2);
+    const size_t mul_per_cand = (mode == BFHE_PAPER ? s : 1) * n * mul_words_per_ct(c);
+    size_t C = (g_scratch_budget / sizeof(u64)) / (per_cand + mul_per_cand);
+    if (C == 0) C = 1;
+    if (C > total) C = total;
+    u64 *fixed, *mul;
+    size_t mw;
+    RC(scratch_for(c, C * per_cand, C * (mode == BFHE_PAPER ? s : 1) * n, &fixed, &mul, &mw));
+    BFHE_CUDA(cudaMemsetAsync(bits_out, 0, (size_t)s * n * ctw * sizeof(u64), st));
+    std::vector<size_t> terms(s, 0);
+    for (size_t cb = 0; cb < total; cb += C) {
+        const int Ct = (int)std::min(C, total - cb);
+        const u64 c_base = c_lo + cb;
+        const size_t m = (size_t)Ct * n;   // chains in this tile
+        u64* D = fixed;                     // [Ct][n]
+        u64* bufs = D + m * ctw;            // pow buffers
+        u64* EQ = bufs + pow_buf_words(c, e, m);
+        RC(launch_sub_const_chains(c, x, D, c_base, Ct, n, st));
+        c->counts[1] += m;
+        RC(pow_impl(c, D, e, EQ, m, bufs, mul, mw, st));
+        RC(launch_lincomb(c, EQ, EQ, nullptr, nullptr, nullptr, LinCoef{1, -1, 0, 0, 0}, 1, m, st));
+        c->counts[1] += m;
+        if (mode == BFHE_PAPER) {
+            u64* TR = EQ + m * ctw;              // [s][Ct][n] trivial bits
+            u64* RP = TR + (size_t)s * m * ctw;  // [s][Ct][n] copies of eq
+            u64* PR = RP + (size_t)s * m * ctw;  // products
+            RC(launch_trivial_bits(c, TR, s, c_base, Ct, n, st));
+            for (uint32_t k = 0; k < s; ++k)
+                BFHE_CUDA(cudaMemcpyAsync(RP + (size_t)k * m * ctw, EQ, m * ctw * sizeof(u64),
+                                          cudaMemcpyDeviceToDevice, st));
+            RC(mul_relin_impl(c, TR, RP, PR, (size_t)s * m, mul, mw, st));
+            c->counts[2] += (uint64_t)s * m;
+            RC(launch_accumulate(c, bits_out, PR, s, c_base, Ct, n, 0, st));
+            for (uint32_t k = 0; k < s; ++k) terms[k] += Ct;
+        } else {
+            RC(launch_accumulate(c, bits_out, EQ, s, c_base, Ct, n, 1, st));
+            for (uint32_t k = 0; k < s; ++k)
+                for (int j = 0; j < Ct; ++j)
+                    if (((c_base + j) >> k) & 1) terms[k] += 1;
+        }
+    }
+    for (uint32_t k = 0; k < s; ++k)
+        if (terms[k] > 1) c->counts[0] += (uint64_t)(terms[k] - 1) * n;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_ntt(bfhe_ctx* c, uint64_t* data, size_t n_polys, uint32_t n_limbs, int inverse, void* stream) {
+    CHECK_CTX(c);
+    if (!data || n_limbs == 0 || n_limbs > c->L) return set_error(BFHE_EINVAL, "bad arguments");
+    if (n_polys == 0) return BFHE_OK;
+    NttIO io = ntt_io(data, data, n_limbs, c->N);
+    if (inverse) return launch_ntt_inv(c, io, (int)n_polys, (int)n_limbs, c->mapQ(), 0, S(stream));
+    return launch_ntt_fwd(c, io, (int)n_polys, (int)n_limbs, c->mapQ(), S(stream));
+}

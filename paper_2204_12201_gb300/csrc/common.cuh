@@ -1,0 +1,202 @@
+// common.cuh -- shared definitions of the bfhe CUDA library (sm_103a).
+//
+// Exact 64-bit modular arithmetic for RNS BFV on the integer pipe: Shoup
+// products for multiplications by precomputed constants (twiddles, CRT
+// constants), Montgomery reduction (REDC) for products of two runtime values
+// and for lazily accumulated sums of them.  Every modulus is an odd prime
+// below 2^60; the NTT keeps values lazily in [0, 4q).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bfhe.h"
+
+typedef uint64_t u64;
+typedef int64_t i64;
+typedef unsigned __int128 u128;
+
+#define BFHE_MAX_L 16
+#define BFHE_MAX_ALPHA 2
+#define BFHE_MAX_PRIMES 64
+
+// ------------------------------------------------------------------ device modular arithmetic
+__host__ __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (u64)(((u128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) {
+    u64 s = a + b;
+    return s >= q ? s - q : s;
+}
+
+__host__ __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// a * w mod q in [0, 2q) for any a < 2^64, w < q, ws = floor(w 2^64 / q) (Shoup).
+__host__ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
+    return a * w - mulhi64(a, ws) * q;
+}
+
+__host__ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
+    u64 r = shoup_lazy(a, w, ws, q);
+    return r >= q ? r - q : r;
+}
+
+// Montgomery reduction: z = hi 2^64 + lo < q 2^64, qinv = -q^-1 mod 2^64;
+// returns z 2^-64 mod q in [0, q).
+__host__ __device__ __forceinline__ u64 redc(u64 hi, u64 lo, u64 q, u64 qinv) {
+    u64 m = lo * qinv;
+    u64 t = hi + mulhi64(m, q) + (lo != 0 ? 1ull : 0ull);
+    return t >= q ? t - q : t;
+}
+
+// 128-bit accumulate of a * b
+__host__ __device__ __forceinline__ void mac128(u64& hi, u64& lo, u64 a, u64 b) {
+    u64 l = a * b;
+    u64 h = mulhi64(a, b);
+    lo += l;
+    hi += h + (lo < l ? 1ull : 0ull);
+}
+
+// x mod q for any 64-bit x, mu = floor(2^64 / q).
+__host__ __device__ __forceinline__ u64 reduce64(u64 x, u64 q, u64 mu) {
+    u64 r = x - mulhi64(x, mu) * q;
+    return r >= q ? r - q : r;
+}
+
+// ------------------------------------------------------------------ exact base extension tables
+// Centred extension of an integer given by residues modulo the source primes
+// s_0..s_{n-1} (S = prod s_i) to target primes T_0..T_{m-1}: Garner's mixed
+// radix digits v_i, a lexicographic compare of (v_{n-1}..v_0) against the
+// digits of (S-1)/2 to decide x > S/2, Horner evaluation mod T_j and a
+// subtraction of [S]_{T_j} for the negative half.
+struct ExtDesc {
+    int n_src, n_dst;
+    const u64* src_q;    // [n_src]
+    const u64* ginv;     // [n_src][n_src]: (i, j<i) -> s_j^-1 mod s_i   (Shoup pair w, ws)
+    const u64* ginv_s;
+    const u64* hdig;     // [n_src] mixed-radix digits of (S-1)/2
+    const u64* dst_q;    // [n_dst]
+    const u64* dst_mu;   // [n_dst] floor(2^64 / T_j)
+    const u64* radix;    // [n_dst][n_src]: [s_i]_{T_j} (Shoup pair)
+    const u64* radix_s;
+    const u64* smod;     // [n_dst]: [S]_{T_j}
+};
+
+// Device-side prime tables of a context, by prime index
+// (0..L-1 data, L..L+alpha-1 special, L+alpha..L+alpha+K-1 auxiliary, last: t).
+struct PrimeTab {
+    const u64* q;        // modulus
+    const u64* qinv;     // -q^-1 mod 2^64
+    const u64* mu;       // floor(2^64 / q)
+    const u64* tw;       // [nP][N] psi^brv(k)   forward twiddles
+    const u64* tw_s;
+    const u64* itw;      // [nP][N] psi^-brv(k)  inverse twiddles
+    const u64* itw_s;
+    const u64* fin;      // [nP][8]: inverse last-stage constants (w, ws) x {ninv, ninv*itw[1]} x {plain, Montgomery}
+};
+
+// limb -> prime index map of a polynomial base: limb < split ? limb : limb + off
+struct LimbMap {
+    int split, off;
+    __host__ __device__ __forceinline__ int operator()(int limb) const { return limb < split ? limb : limb + off; }
+};
+
+// ------------------------------------------------------------------ context
+struct bfhe_ctx {
+    int device = 0;
+    uint32_t N = 0, logN = 0, L = 0, alpha = 0, K = 0, nP = 0, prime_bits = 0;
+    u64 t = 0;
+    std::vector<u64> primes;     // nP: Q, P, B, t
+    std::vector<uint32_t> brv;   // host copy of bit reversal (N)
+
+    void* d_arena = nullptr;     // all constant tables
+    PrimeTab tab{};
+    uint32_t* d_brv = nullptr;   // [N]
+    ExtDesc ext_QB{}, ext_BQ{}, ext_PQ{}, ext_Qt{};
+    // Shoup pair tables: p[i] = w_i, p[n + i] = ws_i
+    const u64* d_tmod = nullptr;    // [nP] [t]_{prime}
+    const u64* d_delta_q = nullptr; // [L]  [Delta]_{q_i}
+    const u64* d_Qinv_b = nullptr;  // [K]  [Q^-1]_{b_j}
+    const u64* d_Pinv_q = nullptr;  // [L]  [P^-1]_{q_i}
+    const u64* d_P_q = nullptr;     // [L]  [P]_{q_i}
+    const u64* d_R2 = nullptr;      // [nP] 2^128 mod prime (Montgomery R^2)
+    u64 Qinv_t = 0;                 // [Q^-1]_t
+    u64 delta_t = 0;
+
+    // keys
+    bool have_keys = false;
+    i64* d_sk = nullptr;         // [N]
+    u64* d_sk_ntt = nullptr;     // [L+alpha][N]
+    u64* d_pk = nullptr;         // [2][L][N] coefficient form
+    u64* d_pk_ntt = nullptr;     // [2][L][N]
+    u64* d_rlk_ntt = nullptr;    // [L][2][L+alpha][N]
+
+    // scratch
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    size_t reserve_n = 0;
+
+    uint64_t counts[4] = {0, 0, 0, 0};
+
+    LimbMap mapQ() const { return LimbMap{(int)L, 0}; }
+    LimbMap mapQP() const { return LimbMap{(int)(L + alpha), 0}; }
+    LimbMap mapQB() const { return LimbMap{(int)L, (int)alpha}; }
+    LimbMap mapT() const { return LimbMap{0, (int)(L + alpha + K)}; }
+    size_t ct_words() const { return (size_t)2 * L * N; }
+};
+
+// ------------------------------------------------------------------ host helpers (host.cu)
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* where);
+#define BFHE_CUDA(call)                                          \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return cuda_check(_e, #call);     \
+    } while (0)
+#define BFHE_LAUNCH_CHECK(where)                                 \
+    do {                                                         \
+        cudaError_t _e = cudaGetLastError();                     \
+        if (_e != cudaSuccess) return cuda_check(_e, where);     \
+    } while (0)
+
+// scratch arena: returns a pointer to at least `bytes` bytes (grows, syncing the device)
+int ctx_scratch(bfhe_ctx* ctx, size_t bytes, void** out);
+// bytes of scratch one mul_relin of n ciphertexts needs
+size_t mul_scratch_bytes(const bfhe_ctx* ctx, size_t n);
+
+// ------------------------------------------------------------------ kernel launchers (ntt.cu)
+// In/out-of-place negacyclic NTT over n_polys x n_limbs limbs.
+// Poly p of a launch is (outer, inner) = (p / n_inner, p % n_inner); a limb's
+// words start at base + outer*os + inner*is + limb*ls (strides in words).
+struct NttIO {
+    const u64* in;
+    u64* out;
+    int n_inner;
+    size_t in_os, in_is, in_ls;
+    size_t out_os, out_is, out_ls;
+};
+// contiguous [n_polys][n_limbs][N] in and out
+inline NttIO ntt_io(const u64* in, u64* out, size_t n_limbs, size_t N) {
+    NttIO io;
+    io.in = in;
+    io.out = out;
+    io.n_inner = 1;
+    io.in_os = io.out_os = n_limbs * N;
+    io.in_is = io.out_is = 0;
+    io.in_ls = io.out_ls = N;
+    return io;
+}
+int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st);
+// mont != 0: the final scale is N^-1 R (undoes one Montgomery factor R^-1 of the inputs)
+int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
+                   cudaStream_t st);
+int ntt_config(int logN, int* log_m, int* log_e);
+void ntt_set_log_e(int log_e);   // tuning override (0 = default)

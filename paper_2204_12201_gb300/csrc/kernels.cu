@@ -1,0 +1,778 @@
+// kernels.cu -- sampling, pointwise, exact RNS and linear kernels of the BFV evaluator.
+//
+// Randomness: Philox4x64-10 (Salmon et al., SC'11) with key (seed, purpose)
+// and counter (block, poly, limb, kind): uniform residues use the word pair
+// (w_hi, w_lo) of block n>>1 at offset 2(n&1) reduced as (w_hi 2^64 + w_lo)
+// mod q; small samples use word n&3 of block n>>2 (kind 1): ternary {0, 1,
+// -1}[w mod 3], centred binomial popcount(w & (2^21-1)) - popcount((w >> 21)
+// & (2^21-1)).
+//
+// Exact RNS: the multiply lifts each input coefficient to the centred range
+// and extends it exactly to the auxiliary base by Garner's mixed-radix
+// conversion (no approximate fast base conversion), and scale-and-round
+// computes round(t d / Q) as y = (t d - r) / Q with r the centred residue of
+// t d mod Q, again by two exact extensions (Q -> B for r, B -> Q for y).
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int grid_for(size_t work) {
+    size_t b = (work + TPB - 1) / TPB;
+    if (b > (size_t)1 << 30) b = (size_t)1 << 30;
+    return (int)(b ? b : 1);
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+__device__ __forceinline__ void philox4x64(u64 c[4], u64 k0, u64 k1) {
+    const u64 M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const u64 W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const u64 lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        const u64 lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        const u64 n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__global__ void k_sample_uniform(u64* out, int n_polys, int n_limbs, LimbMap map, PrimeTab tab, const u64* R2,
+                                 u64 seed, u64 purpose, u64 poly_base, int N) {
+    const size_t half = (size_t)N >> 1;
+    const size_t total = (size_t)n_polys * n_limbs * half;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t blk = idx % half;
+        const int limb = (int)((idx / half) % n_limbs);
+        const int poly = (int)(idx / (half * n_limbs));
+        const int p = map(limb);
+        const u64 q = tab.q[p], qinv = tab.qinv[p], mu = tab.mu[p], r2 = R2[p];
+        u64 c[4] = {(u64)blk, poly_base + (u64)poly, (u64)limb, 0ull};
+        philox4x64(c, seed, purpose);
+        u64* o = out + ((size_t)poly * n_limbs + limb) * N + 2 * blk;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const u64 lo = c[2 * h], hi = reduce64(c[2 * h + 1], q, mu);
+            const u64 t1 = redc(hi, lo, q, qinv);                 // (hi 2^64 + lo) 2^-64
+            o[h] = redc(__umul64hi(t1, r2), t1 * r2, q, qinv);   // * 2^128 * 2^-64
+        }
+    }
+}
+
+__global__ void k_sample_small(i64* out, int n_polys, u64 seed, u64 purpose, u64 poly_base, int cbd, int N) {
+    const size_t quarter = (size_t)N >> 2;
+    const size_t total = (size_t)n_polys * quarter;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t blk = idx % quarter;
+        const int poly = (int)(idx / quarter);
+        u64 c[4] = {(u64)blk, poly_base + (u64)poly, 0ull, 1ull};
+        philox4x64(c, seed, purpose);
+        i64* o = out + (size_t)poly * N + 4 * blk;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const u64 w = c[h];
+            if (cbd) {
+                o[h] = (i64)__popcll(w & 0x1FFFFFull) - (i64)__popcll((w >> 21) & 0x1FFFFFull);
+            } else {
+                const u64 m = w % 3ull;
+                o[h] = m == 0 ? 0 : (m == 1 ? 1 : -1);
+            }
+        }
+    }
+}
+
+__global__ void k_spread(const i64* in, u64* out, int n_polys, int n_limbs, LimbMap map, PrimeTab tab, int N) {
+    const size_t total = (size_t)n_polys * n_limbs * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int limb = (int)((idx / N) % n_limbs);
+        const int poly = (int)(idx / ((size_t)N * n_limbs));
+        const u64 q = tab.q[map(limb)];
+        const i64 v = in[(size_t)poly * N + k];
+        out[idx] = v >= 0 ? (u64)v : q - (u64)(-v);
+    }
+}
+
+// ---------------------------------------------------------------- pointwise (NTT domain)
+__global__ void k_pointwise(const u64* A, const u64* B, u64* out, int n, int polys, int n_limbs, LimbMap map,
+                            PrimeTab tab, PwStrides s, int N) {
+    const size_t total = (size_t)n * polys * n_limbs * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int limb = (int)((idx / N) % n_limbs);
+        const size_t cp = idx / ((size_t)N * n_limbs);
+        const int p = (int)(cp % polys);
+        const size_t c = cp / polys;
+        const int pi = map(limb);
+        const u64 q = tab.q[pi], qinv = tab.qinv[pi];
+        const size_t off = (size_t)limb * N + k;
+        const u64 a = A[c * s.a_cs + p * s.a_ps + off];
+        const u64 b = B[c * s.b_cs + p * s.b_ps + off];
+        out[c * s.o_cs + p * s.o_ps + off] = redc(__umul64hi(a, b), a * b, q, qinv);
+    }
+}
+
+// tensor in place: X[c][0..3] = (a0, a1, b0, b1) -> X[c][0..2] = (d0, d1, d2), Montgomery factor 2^-64
+__global__ void k_tensor(u64* X, int n, int LK, LimbMap map, PrimeTab tab, int N) {
+    const size_t plane = (size_t)LK * N;
+    const size_t total = (size_t)n * plane;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = idx / plane, off = idx % plane;
+        const int limb = (int)(off / N);
+        const int pi = map(limb);
+        const u64 q = tab.q[pi], qinv = tab.qinv[pi];
+        u64* x = X + c * 4 * plane + off;
+        const u64 a0 = x[0], a1 = x[plane], b0 = x[2 * plane], b1 = x[3 * plane];
+        const u64 d0 = redc(__umul64hi(a0, b0), a0 * b0, q, qinv);
+        u64 hi = 0, lo = 0;
+        mac128(hi, lo, a0, b1);
+        mac128(hi, lo, a1, b0);
+        const u64 d1 = redc(hi, lo, q, qinv);
+        const u64 d2 = redc(__umul64hi(a1, b1), a1 * b1, q, qinv);
+        x[0] = d0;
+        x[plane] = d1;
+        x[2 * plane] = d2;
+    }
+}
+
+// key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC)
+template <int CB>
+__global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int L, int QP, PrimeTab tab, int N) {
+    const size_t plane = (size_t)QP * N;   // one digit's limbs
+    const int nchunks = (n + CB - 1) / CB;
+    const size_t total = plane * nchunks;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t off = idx % plane;
+        const int chunk = (int)(idx / plane);
+        const int k = (int)(off / N);
+        const u64 q = tab.q[k], qinv = tab.qinv[k];
+        u64 h0[CB], l0[CB], h1[CB], l1[CB];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) h0[b] = l0[b] = h1[b] = l1[b] = 0;
+        for (int j = 0; j < L; ++j) {
+            const u64 k0 = rlk[((size_t)j * 2 + 0) * plane + off];
+            const u64 k1 = rlk[((size_t)j * 2 + 1) * plane + off];
+#pragma unroll
+            for (int b = 0; b < CB; ++b) {
+                const int c = chunk * CB + b;
+                if (c < n) {
+                    const u64 d = Dg[((size_t)c * L + j) * plane + off];
+                    mac128(h0[b], l0[b], d, k0);
+                    mac128(h1[b], l1[b], d, k1);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+            const int c = chunk * CB + b;
+            if (c < n) {
+                W[((size_t)c * 2 + 0) * plane + off] = redc(h0[b], l0[b], q, qinv);
+                W[((size_t)c * 2 + 1) * plane + off] = redc(h1[b], l1[b], q, qinv);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- exact base extension
+template <int NS>
+__device__ __forceinline__ bool garner(const u64 (&x)[NS], const ExtDesc& d, u64 (&v)[NS]) {
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const u64 si = d.src_q[i];
+        u64 u = x[i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            u64 vj = v[j];
+            vj = vj >= si ? vj - si : vj;
+            u = u >= vj ? u - vj : u + si - vj;
+            u = shoup(u, d.ginv[i * NS + j], d.ginv_s[i * NS + j], si);
+        }
+        v[i] = u;
+    }
+    int state = 0;
+#pragma unroll
+    for (int i = NS - 1; i >= 0; --i) {
+        const u64 h = d.hdig[i];
+        if (state == 0) state = v[i] > h ? 1 : (v[i] < h ? -1 : 0);
+    }
+    return state > 0;   // x > (S-1)/2: the centred value is x - S
+}
+
+// value mod T_j of the centred integer with digits v (SMALL: T may be far below the sources)
+template <int NS, bool SMALL>
+__device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtDesc& d, int j) {
+    const u64 T = d.dst_q[j];
+    const u64 mu = d.dst_mu[j];
+    auto red = [&](u64 a) -> u64 {
+        if (SMALL) return reduce64(a, T, mu);
+        a = a >= T ? a - T : a;
+        return a >= T ? a - T : a;
+    };
+    u64 acc = red(v[NS - 1]);
+#pragma unroll
+    for (int i = NS - 2; i >= 0; --i) {
+        acc = shoup(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T);
+        acc = add_mod(acc, red(v[i]), T);
+    }
+    if (neg) acc = sub_mod(acc, d.smod[j], T);
+    return acc;
+}
+
+// X[pp] (pp = 4c + slot, slots a0 a1 b0 b1): Q limbs copied, B limbs = centred extension
+template <int NS>
+__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int K, ExtDesc ext, int N) {
+    const size_t total = (size_t)n * 4 * N;
+    const int LK = NS + K;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t pp = idx / N;
+        const size_t c = pp >> 2;
+        const int slot = (int)(pp & 3);
+        const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)NS * N + k;
+        u64* dst = X + pp * (size_t)LK * N + k;
+        u64 x[NS], v[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            x[i] = src[(size_t)i * N];
+            dst[(size_t)i * N] = x[i];
+        }
+        const bool neg = garner<NS>(x, ext, v);
+        for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = ext_eval<NS, false>(v, neg, ext, j);
+    }
+}
+
+// scale-and-round of the tensor (X slots 0..2, Q u B limbs) into C3 [n][3][L][N]
+template <int NS, int KS>
+__global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* tmod, int nP,
+                        const u64* Qinv_b, const u64* bq, int N) {
+    const size_t total = (size_t)n * 3 * N;
+    constexpr int LK = NS + KS;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t cp = idx / N;
+        const size_t c = cp / 3;
+        const int comp = (int)(cp % 3);
+        const u64* d = X + (c * 4 + comp) * (size_t)LK * N + k;
+        u64 r[NS], v[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const u64 qi = eQB.src_q[i];
+            r[i] = shoup(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);      // [t d]_{q_i}
+        }
+        const bool neg = garner<NS>(r, eQB, v);
+        u64 y[KS], w[KS];
+#pragma unroll
+        for (int j = 0; j < KS; ++j) {
+            const u64 bj = bq[j];
+            const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
+            const u64 td = shoup(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);
+            const u64 rb = ext_eval<NS, false>(v, neg, eQB, j);
+            y[j] = shoup(sub_mod(td, rb, bj), Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q
+        }
+        const bool negy = garner<KS>(y, eBQ, w);
+        u64* o = C3 + cp * (size_t)NS * N + k;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) o[(size_t)i * N] = ext_eval<KS, false>(w, negy, eBQ, i);
+    }
+}
+
+// out[c][comp] = C3[c][comp] + round(W / P) mod Q, W over Q u P (coefficient form)
+template <int NA>
+__global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, ExtDesc ePQ, const u64* Pinv,
+                          const u64* qtab, int N) {
+    const size_t total = (size_t)n * 2 * N;
+    const int QP = L + NA;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t cp = idx / N;
+        const size_t c = cp >> 1;
+        const int comp = (int)(cp & 1);
+        const u64* w = W + cp * (size_t)QP * N + k;
+        u64 x[NA], v[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) x[a] = w[(size_t)(L + a) * N];
+        const bool neg = garner<NA>(x, ePQ, v);
+        const u64* cin = C3 + (c * 3 + comp) * (size_t)L * N + k;
+        u64* o = out + cp * (size_t)L * N + k;
+        for (int i = 0; i < L; ++i) {
+            const u64 qi = qtab[i];
+            const u64 e = ext_eval<NA, false>(v, neg, ePQ, i);
+            const u64 y = shoup(sub_mod(w[(size_t)i * N], e, qi), Pinv[i], Pinv[L + i], qi);
+            o[(size_t)i * N] = add_mod(cin[(size_t)i * N], y, qi);
+        }
+    }
+}
+
+// decrypt: m = [-r Q^-1]_t with r the centred [t (c0 + c1 s)]_Q
+template <int NS>
+__global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc eQt, const u64* tmod, int nP,
+                             u64 Qinv_t, int N) {
+    const size_t total = (size_t)n * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t c = idx / N;
+        u64 r[NS], v[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const u64 qi = eQt.src_q[i];
+            const u64 vi = add_mod(V[(c * NS + i) * N + k], ct[(c * 2 * NS + i) * N + k], qi);
+            r[i] = shoup(vi, tmod[i], tmod[nP + i], qi);
+        }
+        const bool neg = garner<NS>(r, eQt, v);
+        const u64 t = eQt.dst_q[0];
+        const u64 rho = ext_eval<NS, true>(v, neg, eQt, 0);        // [r]_t
+        const u64 mneg = rho == 0 ? 0 : t - rho;
+        M[idx] = (mneg * Qinv_t) % t;
+    }
+}
+
+// ---------------------------------------------------------------- encode/decode, encrypt, keygen
+__global__ void k_permute(const u64* in, u64* out, const uint32_t* brv, int n, int scatter, int N) {
+    const size_t total = (size_t)n * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % N);
+        const size_t base = idx - j;
+        if (scatter)
+            out[base + brv[j]] = in[idx];
+        else
+            out[idx] = in[base + brv[j]];
+    }
+}
+
+__global__ void k_enc_finish(u64* ct, const u64* M, const i64* e1, const i64* e2, int n, int L, const u64* qtab,
+                             const u64* delta, int N) {
+    const size_t total = (size_t)n * L * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int i = (int)((idx / N) % L);
+        const size_t c = idx / ((size_t)N * L);
+        const u64 q = qtab[i];
+        const u64 m = M[c * N + k];
+        const i64 a = e1[c * N + k], b = e2[c * N + k];
+        u64* c0 = ct + (c * 2 * L + i) * N + k;
+        u64* c1 = c0 + (size_t)L * N;
+        u64 v = add_mod(*c0, shoup(m, delta[i], delta[L + i], q), q);
+        v = a >= 0 ? add_mod(v, (u64)a, q) : sub_mod(v, (u64)(-a), q);
+        *c0 = v;
+        u64 w = *c1;
+        *c1 = b >= 0 ? add_mod(w, (u64)b, q) : sub_mod(w, (u64)(-b), q);
+    }
+}
+
+// out = -(as + e) [+ [P]_{q_j} s2 on limb j of poly j when gadget]
+__global__ void k_neg_add_small(const u64* as, const i64* e, u64* out, int n_polys, int n_limbs, LimbMap map,
+                                PrimeTab tab, const u64* s2, int gadget, const u64* Pq, int L, int N) {
+    const size_t total = (size_t)n_polys * n_limbs * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int limb = (int)((idx / N) % n_limbs);
+        const int poly = (int)(idx / ((size_t)N * n_limbs));
+        const u64 q = tab.q[map(limb)];
+        const i64 ev = e[(size_t)poly * N + k];
+        u64 v = as[idx];
+        v = ev >= 0 ? add_mod(v, (u64)ev, q) : sub_mod(v, (u64)(-ev), q);
+        v = v == 0 ? 0 : q - v;
+        if (gadget && limb == poly) {
+            const u64 g = shoup(s2[(size_t)limb * N + k], Pq[limb], Pq[L + limb], q);
+            v = add_mod(v, g, q);
+        }
+        out[idx] = v;
+    }
+}
+
+// ---------------------------------------------------------------- linear ops
+__device__ __forceinline__ u64 apply(u64 acc, u64 v, int c, u64 q) {
+    switch (c) {
+        case 1: return add_mod(acc, v, q);
+        case 2: return add_mod(add_mod(acc, v, q), v, q);
+        case -1: return sub_mod(acc, v, q);
+        case -2: return sub_mod(sub_mod(acc, v, q), v, q);
+        default: return acc;
+    }
+}
+
+__constant__ int c_gate_coef[8][5] = {
+    // cc  cx  cy  cz  cp
+    {0, 0, 0, 0, 1},     // AND  = xy
+    {0, 1, 1, 0, -1},    // OR   = x + y - xy
+    {0, 1, 1, 0, -2},    // XOR  = x + y - 2xy
+    {1, 0, 0, 0, -1},    // NAND = 1 - xy
+    {1, -1, -1, 0, 1},   // NOR  = 1 - (x + y - xy)
+    {1, -1, -1, 0, 2},   // XNOR = 1 - (x + y - 2xy)
+    {1, -1, 0, 0, 0},    // NOT  = 1 - x
+    {0, 0, 0, 1, 1},     // MUX  = x (y - z) + z
+};
+
+__device__ __forceinline__ u64 lin_word(int cc, int cx, int cy, int cz, int cp, u64 cval, const u64* x,
+                                        const u64* y, const u64* z, const u64* p, size_t o, int comp, int k,
+                                        u64 q, u64 dw, u64 dws) {
+    u64 acc = 0;
+    if (cc != 0 && comp == 0 && k == 0) acc = apply(acc, shoup(cval, dw, dws, q), cc, q);
+    if (cx) acc = apply(acc, x[o], cx, q);
+    if (cy) acc = apply(acc, y[o], cy, q);
+    if (cz) acc = apply(acc, z[o], cz, q);
+    if (cp) acc = apply(acc, p[o], cp, q);
+    return acc;
+}
+
+__global__ void k_lincomb(u64* out, const u64* x, const u64* y, const u64* z, const u64* p, LinCoef cf, u64 cval,
+                          size_t n, int L, const u64* qtab, const u64* delta, int N) {
+    const size_t total = n * 2 * L * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const int i = (int)((idx / N) % L);
+        const int comp = (int)((idx / ((size_t)N * L)) & 1);
+        out[idx] = lin_word(cf.cc, cf.cx, cf.cy, cf.cz, cf.cp, cval, x, y, z, p, idx, comp, k, qtab[i], delta[i],
+                            delta[L + i]);
+    }
+}
+
+struct ScalarPairs {
+    u64 w[BFHE_MAX_L], ws[BFHE_MAX_L];
+};
+
+__global__ void k_mul_scalar(const u64* a, u64* out, ScalarPairs sp, size_t n, int L, const u64* qtab, int N) {
+    const size_t total = n * 2 * L * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)((idx / N) % L);
+        out[idx] = shoup(a[idx], sp.w[i], sp.ws[i], qtab[i]);
+    }
+}
+
+// Listing 5: r = v[s-1]; r += r + v[i], i = s-2 .. 0
+__global__ void k_horner(const u64* bits, uint32_t s, u64* out, size_t n, int L, const u64* qtab, int N) {
+    const size_t words = n * 2 * L * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < words;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const u64 q = qtab[(idx / N) % L];
+        u64 r = bits[(size_t)(s - 1) * words + idx];
+        for (int i = (int)s - 2; i >= 0; --i) r = add_mod(r, add_mod(r, bits[(size_t)i * words + idx], q), q);
+        out[idx] = r;
+    }
+}
+
+// gather gate operands: A[g] = wires[x], B[g] = wires[y] (MUX: wires[y] - wires[z])
+__global__ void k_gather_ops(u64* A, u64* B, const u64* wires, size_t ctw, const int32_t* table, int n_gates,
+                             int L, const u64* qtab, int N) {
+    const size_t total = (size_t)n_gates * ctw;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(idx / ctw);
+        const size_t o = idx % ctw;
+        const int32_t* e = table + 5 * g;
+        const u64 q = qtab[(o / N) % L];
+        A[idx] = wires[(size_t)e[1] * ctw + o];
+        const u64 yv = wires[(size_t)e[2] * ctw + o];
+        B[idx] = e[0] == BFHE_MUX ? sub_mod(yv, wires[(size_t)e[3] * ctw + o], q) : yv;
+    }
+}
+
+// gate epilogue: wires[out] = lin(gate)(x, y, z, prod[g]); gates g >= n_mul (NOT) have no product
+__global__ void k_gate_epilogue(u64* wires, size_t ctw, const int32_t* table, int n_gates, int n_mul,
+                                const u64* prod, int L, const u64* qtab, const u64* delta, int N) {
+    const size_t total = (size_t)n_gates * ctw;
+    const size_t per_comp = (size_t)L * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(idx / ctw);
+        const size_t o = idx % ctw;
+        const int32_t* e = table + 5 * g;
+        const int* cf = c_gate_coef[e[0] & 7];
+        const int i = (int)((o / N) % L);
+        const int k = (int)(o % N);
+        const int comp = (int)((o / per_comp) & 1);
+        const u64* x = wires + (size_t)e[1] * ctw;
+        const u64* y = wires + (size_t)e[2] * ctw;
+        const u64* z = wires + (size_t)e[3] * ctw;
+        const u64* p = g < n_mul ? prod + (size_t)g * ctw : nullptr;
+        wires[(size_t)e[4] * ctw + o] =
+            lin_word(cf[0], cf[1], cf[2], cf[3], g < n_mul ? cf[4] : 0, 1, x, y, z, p, o, comp, k, qtab[i],
+                     delta[i], delta[L + i]);
+    }
+}
+
+// trivial ciphertexts (Delta bit_k(c_base + c), 0), layout [s][C][n][2][L][N]
+__global__ void k_trivial_bits(u64* out, uint32_t s, u64 c_base, int C, size_t n, int L, const u64* delta, int N) {
+    const size_t ctw = (size_t)2 * L * N;
+    const size_t total = (size_t)s * C * n * ctw;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t o = idx % ctw;
+        const size_t rest = idx / ctw;
+        const int c = (int)((rest / n) % C);
+        const int kbit = (int)(rest / (n * C));
+        const int i = (int)(o / N);   // < L only for c0
+        u64 v = 0;
+        if (o < (size_t)L * N && (o % N) == 0 && (((c_base + c) >> kbit) & 1)) v = delta[i];
+        out[idx] = v;
+    }
+}
+
+// bits[k][i] += sum over c of src (PAPER: src [s][C][n]; SELECT: src [C][n], only if bit k of c)
+__global__ void k_accumulate(u64* bits, const u64* src, uint32_t s, u64 c_base, int C, size_t n, int select,
+                             int L, const u64* qtab, int N) {
+    const size_t ctw = (size_t)2 * L * N;
+    const size_t words = n * ctw;
+    const size_t total = (size_t)s * words;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int kbit = (int)(idx / words);
+        const size_t w = idx % words;
+        const u64 q = qtab[(w / N) % L];
+        u64 acc = bits[idx];
+        for (int c = 0; c < C; ++c) {
+            if (select) {
+                if (((c_base + c) >> kbit) & 1) acc = add_mod(acc, src[(size_t)c * words + w], q);
+            } else {
+                acc = add_mod(acc, src[((size_t)kbit * C + c) * words + w], q);
+            }
+        }
+        bits[idx] = acc;
+    }
+}
+
+// out[c][i] = x[i] - (c_base + c)   (layout [C][n])
+__global__ void k_sub_const_chains(const u64* x, u64* out, u64 c_base, int C, size_t n, int L, const u64* qtab,
+                                   const u64* delta, u64 t, int N) {
+    const size_t ctw = (size_t)2 * L * N;
+    const size_t words = n * ctw;
+    const size_t total = (size_t)C * words;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / words);
+        const size_t w = idx % words;
+        const size_t o = w % ctw;
+        u64 v = x[w];
+        if (o < (size_t)L * N && (o % N) == 0) {
+            const int i = (int)(o / N);
+            const u64 q = qtab[i];
+            const u64 cv = (c_base + c) % t;
+            v = sub_mod(v, shoup(cv, delta[i], delta[L + i], q), q);
+        }
+        out[idx] = v;
+    }
+}
+
+}  // namespace
+
+// ================================================================== launchers
+#define LAUNCH(kern, work, ...)                                                   \
+    do {                                                                          \
+        auto* _kfn = kern;                                                        \
+        _kfn<<<grid_for(work), TPB, 0, st>>>(__VA_ARGS__);                       \
+        BFHE_LAUNCH_CHECK(#kern);                                                \
+    } while (0)
+
+int launch_sample_uniform(const bfhe_ctx* ctx, u64* out, int n_polys, int n_limbs, LimbMap map, u64 seed,
+                          u64 purpose, u64 poly_base, cudaStream_t st) {
+    LAUNCH(k_sample_uniform, (size_t)n_polys * n_limbs * ctx->N / 2, out, n_polys, n_limbs, map, ctx->tab, ctx->d_R2,
+           seed, purpose, poly_base, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_sample_small(const bfhe_ctx* ctx, i64* out, int n_polys, u64 seed, u64 purpose, u64 poly_base, int cbd,
+                        cudaStream_t st) {
+    LAUNCH(k_sample_small, (size_t)n_polys * ctx->N / 4, out, n_polys, seed, purpose, poly_base, cbd, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_spread(const bfhe_ctx* ctx, const i64* in, u64* out, int n_polys, int n_limbs, LimbMap map,
+                  cudaStream_t st) {
+    LAUNCH(k_spread, (size_t)n_polys * n_limbs * ctx->N, in, out, n_polys, n_limbs, map, ctx->tab, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_pointwise(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* out, int n, int polys, int n_limbs,
+                     LimbMap map, PwStrides s, cudaStream_t st) {
+    LAUNCH(k_pointwise, (size_t)n * polys * n_limbs * ctx->N, A, B, out, n, polys, n_limbs, map, ctx->tab, s,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, cudaStream_t st) {
+    const int LK = (int)(ctx->L + ctx->K);
+    LAUNCH(k_tensor, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
+    const int QP = (int)(ctx->L + ctx->alpha);
+    constexpr int CB = 4;
+    const size_t work = (size_t)QP * ctx->N * ((n + CB - 1) / CB);
+    LAUNCH(k_inner<CB>, work, Dg, ctx->d_rlk_ntt, W, n, (int)ctx->L, QP, ctx->tab, (int)ctx->N);
+    return BFHE_OK;
+}
+
+template <int NS>
+int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, cudaStream_t st) {
+    const size_t work = (size_t)n * 4 * ctx->N;
+    LAUNCH(k_modup<NS>, work, A, B, X, n, (int)ctx->K, ctx->ext_QB, (int)ctx->N);
+    return BFHE_OK;
+}
+
+template <int NS>
+int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
+    const size_t work = (size_t)n * 3 * ctx->N;
+    const u64* bq = ctx->tab.q + ctx->L + ctx->alpha;
+    LAUNCH((k_scale<NS, NS + 1>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
+           ctx->d_Qinv_b, bq, (int)ctx->N);
+    return BFHE_OK;
+}
+
+template <int NS>
+int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
+    const size_t work = (size_t)n * ctx->N;
+    LAUNCH(k_dec_finish<NS>, work, V, ct, M, n, ctx->ext_Qt, ctx->d_tmod, (int)ctx->nP, ctx->Qinv_t, (int)ctx->N);
+    return BFHE_OK;
+}
+
+#define SWITCH_L(Lv, FN, ...)                                                                                  \
+    switch (Lv) {                                                                                              \
+        case 1: return FN<1>(__VA_ARGS__);                                                                     \
+        case 2: return FN<2>(__VA_ARGS__);                                                                     \
+        case 3: return FN<3>(__VA_ARGS__);                                                                     \
+        case 4: return FN<4>(__VA_ARGS__);                                                                     \
+        case 5: return FN<5>(__VA_ARGS__);                                                                     \
+        case 6: return FN<6>(__VA_ARGS__);                                                                     \
+        case 7: return FN<7>(__VA_ARGS__);                                                                     \
+        case 8: return FN<8>(__VA_ARGS__);                                                                     \
+        case 9: return FN<9>(__VA_ARGS__);                                                                     \
+        case 10: return FN<10>(__VA_ARGS__);                                                                   \
+        case 11: return FN<11>(__VA_ARGS__);                                                                   \
+        case 12: return FN<12>(__VA_ARGS__);                                                                   \
+        case 13: return FN<13>(__VA_ARGS__);                                                                   \
+        case 14: return FN<14>(__VA_ARGS__);                                                                   \
+        case 15: return FN<15>(__VA_ARGS__);                                                                   \
+        case 16: return FN<16>(__VA_ARGS__);                                                                   \
+        default: return set_error(BFHE_EINVAL, "unsupported number of data primes");                         \
+    }
+
+int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, cudaStream_t st) {
+    SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, st)
+}
+
+int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
+    if (ctx->K != ctx->L + 1) return set_error(BFHE_EINVAL, "auxiliary base must have L+1 primes");
+    SWITCH_L(ctx->L, run_scale, ctx, X, C3, n, st)
+}
+
+int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st) {
+    const size_t work = (size_t)n * 2 * ctx->N;
+    if (ctx->alpha == 1)
+        LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
+    else if (ctx->alpha == 2)
+        LAUNCH(k_moddown<2>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
+    else
+        return set_error(BFHE_EINVAL, "alpha must be 1 or 2");
+    return BFHE_OK;
+}
+
+int launch_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
+    SWITCH_L(ctx->L, run_dec_finish, ctx, V, ct, M, n, st)
+}
+
+int launch_permute(const bfhe_ctx* ctx, const u64* in, u64* out, int n, int scatter, cudaStream_t st) {
+    LAUNCH(k_permute, (size_t)n * ctx->N, in, out, ctx->d_brv, n, scatter, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_enc_finish(const bfhe_ctx* ctx, u64* ct, const u64* M, const i64* e1, const i64* e2, int n,
+                      cudaStream_t st) {
+    LAUNCH(k_enc_finish, (size_t)n * ctx->L * ctx->N, ct, M, e1, e2, n, (int)ctx->L, ctx->tab.q, ctx->d_delta_q,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_neg_add_small(const bfhe_ctx* ctx, const u64* as, const i64* e, u64* out, int n_polys, int n_limbs,
+                         LimbMap map, const u64* s2, int gadget, cudaStream_t st) {
+    LAUNCH(k_neg_add_small, (size_t)n_polys * n_limbs * ctx->N, as, e, out, n_polys, n_limbs, map, ctx->tab, s2,
+           gadget, ctx->d_P_q, (int)ctx->L, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_lincomb(const bfhe_ctx* ctx, u64* out, const u64* x, const u64* y, const u64* z, const u64* p,
+                   LinCoef cf, u64 cval, size_t n, cudaStream_t st) {
+    LAUNCH(k_lincomb, n * ctx->ct_words(), out, x, y, z, p, cf, cval, n, (int)ctx->L, ctx->tab.q, ctx->d_delta_q,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_mul_scalar(const bfhe_ctx* ctx, const u64* a, u64 c, u64* out, size_t n, cudaStream_t st) {
+    ScalarPairs sp;
+    for (uint32_t i = 0; i < ctx->L; ++i) {
+        const u64 q = ctx->primes[i];
+        const u64 w = c % q;
+        sp.w[i] = w;
+        sp.ws[i] = (u64)(((u128)w << 64) / q);
+    }
+    LAUNCH(k_mul_scalar, n * ctx->ct_words(), a, out, sp, n, (int)ctx->L, ctx->tab.q, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_horner(const bfhe_ctx* ctx, const u64* bits, uint32_t s, u64* out, size_t n, cudaStream_t st) {
+    LAUNCH(k_horner, n * ctx->ct_words(), bits, s, out, n, (int)ctx->L, ctx->tab.q, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_gather(const bfhe_ctx* ctx, u64* dst, const u64* wires, size_t n, const int32_t* table, int n_gates,
+                  int field, int sub_field, cudaStream_t st) {
+    // field/sub_field are unused by this layout: dst holds A then B ([2][n_gates][n] ciphertexts)
+    (void)field;
+    (void)sub_field;
+    const size_t ctw = n * ctx->ct_words();
+    u64* A = dst;
+    u64* B = dst + (size_t)n_gates * ctw;
+    LAUNCH(k_gather_ops, (size_t)n_gates * ctw, A, B, wires, ctw, table, n_gates, (int)ctx->L, ctx->tab.q,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_gate_epilogue(const bfhe_ctx* ctx, u64* wires, size_t n, const int32_t* table, int n_gates,
+                         const u64* prod, int n_mul, cudaStream_t st) {
+    const size_t ctw = n * ctx->ct_words();
+    LAUNCH(k_gate_epilogue, (size_t)n_gates * ctw, wires, ctw, table, n_gates, n_mul, prod, (int)ctx->L, ctx->tab.q,
+           ctx->d_delta_q, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_trivial_bits(const bfhe_ctx* ctx, u64* out, uint32_t s, u64 c_base, int C, size_t n, cudaStream_t st) {
+    LAUNCH(k_trivial_bits, (size_t)s * C * n * ctx->ct_words(), out, s, c_base, C, n, (int)ctx->L, ctx->d_delta_q,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s, u64 c_base, int C, size_t n,
+                      int select, cudaStream_t st) {
+    LAUNCH(k_accumulate, (size_t)s * n * ctx->ct_words(), bits, src, s, c_base, C, n, select, (int)ctx->L, ctx->tab.q,
+           (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, int C, size_t n,
+                            cudaStream_t st) {
+    LAUNCH(k_sub_const_chains, (size_t)C * n * ctx->ct_words(), x, out, c_base, C, n, (int)ctx->L, ctx->tab.q,
+           ctx->d_delta_q, ctx->t, (int)ctx->N);
+    return BFHE_OK;
+}

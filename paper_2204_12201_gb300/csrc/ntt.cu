@@ -1,0 +1,373 @@
+// ntt.cu -- negacyclic NTT / INTT over Z_q[X]/(X^N + 1) per RNS prime.
+//
+// Forward: Cooley-Tukey with merged psi twiddles (natural order in, bit-
+// reversed evaluation order out); butterfly on bit b of the index with
+// twiddle psi^brv((N + j) >> (b + 1)); Harvey's lazy butterflies keep values
+// in [0, 4q) and one Shoup product per butterfly.  Inverse: Gentleman-Sande
+// with psi^-brv twiddles, values in [0, 2q), the N^-1 scale (times R = 2^64
+// when the inputs carry a Montgomery factor) merged into the last stage.
+//
+// One CTA transforms a block of M = 2^LOG_M <= 16384 consecutive words of a
+// limb held in shared memory; each thread keeps E = 2^LOG_E words in
+// registers and runs up to LOG_E radix-2 stages on them per pass, with one
+// padded shared-memory exchange (one pad word per 16, conflict-free for
+// every window) and one barrier between passes.  The first pass reads global
+// memory directly (coalesced: lanes differ in the low index bits) and the
+// last pass writes it directly (forward: E consecutive words per thread as
+// 16-byte stores; inverse: coalesced).  For N = 2M the outermost stage runs
+// as a separate elementwise pass.
+#include "common.cuh"
+
+namespace {
+
+__device__ __forceinline__ int phys(int j) { return j + (j >> 4); }
+
+struct NttArgs {
+    const u64* in;
+    u64* out;
+    int n_inner;
+    size_t in_os, in_is, in_ls, out_os, out_is, out_ls;
+    int n_limbs;
+    LimbMap map;
+    PrimeTab tab;
+    int N, logN;
+    int mont;
+};
+
+struct LimbPtrs {
+    const u64* in;
+    u64* out;
+    int p;
+};
+
+__device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx, size_t sub_off) {
+    const int limb = bx % a.n_limbs;
+    const int poly = bx / a.n_limbs;
+    const int outer = poly / a.n_inner, inner = poly % a.n_inner;
+    LimbPtrs r;
+    r.in = a.in + outer * a.in_os + inner * a.in_is + limb * a.in_ls + sub_off;
+    r.out = a.out + outer * a.out_os + inner * a.out_is + limb * a.out_ls + sub_off;
+    r.p = a.map(limb);
+    return r;
+}
+
+// ---------------------------------------------------------------- forward stages
+template <int LOG_E, int W_LO, int HI, int LO>
+__device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u64* __restrict__ tw,
+                                           const u64* __restrict__ tws, u64 q) {
+    constexpr int E = 1 << LOG_E;
+    const u64 q2 = q << 1;
+#pragma unroll
+    for (int st = 0; st <= HI - LO; ++st) {
+        const int b = HI - st;
+        const int h = b - W_LO;
+        const u64 base = jb >> (b + 1);
+#pragma unroll
+        for (int g = 0; g < (E >> (h + 1)); ++g) {
+            const u64 w = __ldg(tw + base + g);
+            const u64 ws = __ldg(tws + base + g);
+#pragma unroll
+            for (int r = 0; r < (1 << h); ++r) {
+                const int e = (g << (h + 1)) | r;
+                const int e2 = e | (1 << h);
+                u64 X = x[e];
+                X = X >= q2 ? X - q2 : X;
+                const u64 T = shoup_lazy(x[e2], w, ws, q);
+                x[e] = X + T;
+                x[e2] = X - T + q2;
+            }
+        }
+    }
+}
+
+template <int LOG_M, int LOG_E, int P>
+__device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const u64* tw,
+                                         const u64* tws, u64 q, const u64* in, u64* out) {
+    constexpr int E = 1 << LOG_E;
+    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
+    constexpr int HI = LOG_M - 1 - P * LOG_E;
+    constexpr int LO = (HI - LOG_E + 1) > 0 ? (HI - LOG_E + 1) : 0;
+    constexpr int W_LO = LO;
+    const int base = (tid & ((1 << W_LO) - 1)) | ((tid >> W_LO) << (W_LO + LOG_E));
+    if (P == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = in[base + (e << W_LO)];
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
+    }
+    fwd_stages<LOG_E, W_LO, HI, LO>(x, jglob + base, tw, tws, q);
+    if constexpr (P + 1 < NPASS) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        __syncthreads();
+        fwd_pass<LOG_M, LOG_E, P + 1>(x, sm, tid, jglob, tw, tws, q, in, out);
+    } else {
+        // W_LO == 0 here: E consecutive words per thread
+        const u64 q2 = q << 1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            u64 v = x[e];
+            v = v >= q2 ? v - q2 : v;
+            x[e] = v >= q ? v - q : v;
+        }
+        ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + base);
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) o2[e] = make_ulonglong2(x[2 * e], x[2 * e + 1]);
+    }
+}
+
+template <int LOG_M, int LOG_E>
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_fwd(NttArgs a) {
+    extern __shared__ u64 sm[];
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
+    const u64 q = a.tab.q[lp.p];
+    const u64* tw = a.tab.tw + (size_t)lp.p * a.N;
+    const u64* tws = a.tab.tw_s + (size_t)lp.p * a.N;
+    const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
+    u64 x[1 << LOG_E];
+    fwd_pass<LOG_M, LOG_E, 0>(x, sm, threadIdx.x, jglob, tw, tws, q, lp.in, lp.out);
+}
+
+// outermost stage (bit logN - 1) for N = 2M, elementwise; inputs < 4q, outputs lazily < 4q
+__global__ void k_ntt_fwd_top(NttArgs a) {
+    const int half = a.N >> 1;
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, 0);
+    const u64 q = a.tab.q[lp.p], q2 = q << 1;
+    const u64 w = a.tab.tw[(size_t)lp.p * a.N + 1], ws = a.tab.tw_s[(size_t)lp.p * a.N + 1];
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
+        u64 X = lp.in[j];
+        X = X >= q2 ? X - q2 : X;
+        const u64 T = shoup_lazy(lp.in[j + half], w, ws, q);
+        lp.out[j] = X + T;
+        lp.out[j + half] = X - T + q2;
+    }
+}
+
+// ---------------------------------------------------------------- inverse stages
+template <int LOG_E, int W_LO, int LO, int HI, bool SCALE_TOP>
+__device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const u64* __restrict__ itw,
+                                           const u64* __restrict__ itws, u64 q, const u64* fin) {
+    constexpr int E = 1 << LOG_E;
+    const u64 q2 = q << 1;
+#pragma unroll
+    for (int st = 0; st <= HI - LO; ++st) {
+        const int b = LO + st;
+        const int h = b - W_LO;
+        const u64 base = jb >> (b + 1);
+        if (SCALE_TOP && b == HI) {
+            const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
+#pragma unroll
+            for (int g = 0; g < (E >> (h + 1)); ++g) {
+#pragma unroll
+                for (int r = 0; r < (1 << h); ++r) {
+                    const int e = (g << (h + 1)) | r;
+                    const int e2 = e | (1 << h);
+                    const u64 X = x[e], Y = x[e2];
+                    x[e] = shoup(X + Y, n0, n0s, q);
+                    x[e2] = shoup(X - Y + q2, n1, n1s, q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < (E >> (h + 1)); ++g) {
+                const u64 w = __ldg(itw + base + g);
+                const u64 ws = __ldg(itws + base + g);
+#pragma unroll
+                for (int r = 0; r < (1 << h); ++r) {
+                    const int e = (g << (h + 1)) | r;
+                    const int e2 = e | (1 << h);
+                    const u64 X = x[e], Y = x[e2];
+                    u64 S = X + Y;
+                    S = S >= q2 ? S - q2 : S;
+                    x[e] = S;
+                    x[e2] = shoup_lazy(X - Y + q2, w, ws, q);
+                }
+            }
+        }
+    }
+}
+
+template <int LOG_M, int LOG_E, int P, bool FULL>
+__device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const u64* itw,
+                                         const u64* itws, u64 q, const u64* fin, const u64* in, u64* out) {
+    constexpr int E = 1 << LOG_E;
+    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
+    constexpr int LO = P * LOG_E;
+    constexpr int HI = (LO + LOG_E - 1) < (LOG_M - 1) ? (LO + LOG_E - 1) : (LOG_M - 1);
+    constexpr int W_LO = (HI - LO + 1 == LOG_E) ? LO : (LOG_M - LOG_E);
+    const int base = (tid & ((1 << W_LO) - 1)) | ((tid >> W_LO) << (W_LO + LOG_E));
+    if (P == 0) {
+        // W_LO == 0: E consecutive words per thread
+        const ulonglong2* i2 = reinterpret_cast<const ulonglong2*>(in + base);
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) {
+            const ulonglong2 v = i2[e];
+            x[2 * e] = v.x;
+            x[2 * e + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
+    }
+    constexpr bool LAST = (P + 1 == NPASS);
+    inv_stages<LOG_E, W_LO, LO, HI, FULL && LAST>(x, jglob + base, itw, itws, q, fin);
+    if constexpr (!LAST) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        __syncthreads();
+        inv_pass<LOG_M, LOG_E, P + 1, FULL>(x, sm, tid, jglob, itw, itws, q, fin, in, out);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) out[base + (e << W_LO)] = x[e];
+    }
+}
+
+template <int LOG_M, int LOG_E, bool FULL>
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_inv(NttArgs a) {
+    extern __shared__ u64 sm[];
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
+    const u64 q = a.tab.q[lp.p];
+    const u64* itw = a.tab.itw + (size_t)lp.p * a.N;
+    const u64* itws = a.tab.itw_s + (size_t)lp.p * a.N;
+    const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
+    const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
+    u64 x[1 << LOG_E];
+    inv_pass<LOG_M, LOG_E, 0, FULL>(x, sm, threadIdx.x, jglob, itw, itws, q, fin, lp.in, lp.out);
+}
+
+// outermost inverse stage with the N^-1 scale, for N = 2M; inputs < 2q, outputs canonical
+__global__ void k_ntt_inv_top(NttArgs a) {
+    const int half = a.N >> 1;
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, 0);
+    const u64 q = a.tab.q[lp.p], q2 = q << 1;
+    const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
+    const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
+        const u64 X = lp.out[j], Y = lp.out[j + half];
+        lp.out[j] = shoup(X + Y, n0, n0s, q);
+        lp.out[j + half] = shoup(X - Y + q2, n1, n1s, q);
+    }
+}
+
+int g_log_e_override = 0;
+
+template <int LOG_M, int LOG_E>
+int run_fwd(const NttArgs& a, int blocks, int subs, cudaStream_t st) {
+    constexpr int T = 1 << (LOG_M - LOG_E);
+    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
+    const size_t smem = NPASS > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
+    static bool attr = false;
+    if (!attr) {
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        attr = true;
+    }
+    k_ntt_fwd<LOG_M, LOG_E><<<dim3(blocks, subs), T, smem, st>>>(a);
+    BFHE_LAUNCH_CHECK("k_ntt_fwd");
+    return BFHE_OK;
+}
+
+template <int LOG_M, int LOG_E, bool FULL>
+int run_inv(const NttArgs& a, int blocks, int subs, cudaStream_t st) {
+    constexpr int T = 1 << (LOG_M - LOG_E);
+    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
+    const size_t smem = NPASS > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
+    static bool attr = false;
+    if (!attr) {
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        attr = true;
+    }
+    k_ntt_inv<LOG_M, LOG_E, FULL><<<dim3(blocks, subs), T, smem, st>>>(a);
+    BFHE_LAUNCH_CHECK("k_ntt_inv");
+    return BFHE_OK;
+}
+
+NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map, int mont) {
+    NttArgs a;
+    a.in = io.in;
+    a.out = io.out;
+    a.n_inner = io.n_inner > 0 ? io.n_inner : 1;
+    a.in_os = io.in_os;
+    a.in_is = io.in_is;
+    a.in_ls = io.in_ls;
+    a.out_os = io.out_os;
+    a.out_is = io.out_is;
+    a.out_ls = io.out_ls;
+    a.n_limbs = n_limbs;
+    a.map = map;
+    a.tab = ctx->tab;
+    a.N = (int)ctx->N;
+    a.logN = (int)ctx->logN;
+    a.mont = mont;
+    return a;
+}
+
+}  // namespace
+
+void ntt_set_log_e(int log_e) { g_log_e_override = log_e; }
+
+int ntt_config(int logN, int* log_m, int* log_e) {
+    *log_m = logN > 14 ? 14 : logN;
+    int e = 4;
+    if (g_log_e_override >= 3 && g_log_e_override <= 5) e = g_log_e_override;
+    *log_e = e;
+    return BFHE_OK;
+}
+
+#define FWD_CASE(LM, LE) \
+    if (log_m == LM && log_e == LE) return run_fwd<LM, LE>(a, blocks, subs, st);
+#define INV_CASE(LM, LE)                                                        \
+    if (log_m == LM && log_e == LE)                                              \
+        return full ? run_inv<LM, LE, true>(a, blocks, subs, st) : run_inv<LM, LE, false>(a, blocks, subs, st);
+
+int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st) {
+    if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
+    int log_m, log_e;
+    ntt_config((int)ctx->logN, &log_m, &log_e);
+    NttArgs a = make_args(ctx, io, n_limbs, map, 0);
+    const int blocks = n_polys * n_limbs;
+    const int subs = (int)(ctx->N >> log_m);
+    if (subs == 2) {
+        k_ntt_fwd_top<<<dim3(blocks, 8), 256, 0, st>>>(a);
+        BFHE_LAUNCH_CHECK("k_ntt_fwd_top");
+        // the block pass continues in place on the output
+        a.in = a.out;
+        a.in_os = a.out_os;
+        a.in_is = a.out_is;
+        a.in_ls = a.out_ls;
+    } else if (subs != 1) {
+        return set_error(BFHE_EINVAL, "unsupported ring degree");
+    }
+    FWD_CASE(10, 3) FWD_CASE(10, 4) FWD_CASE(10, 5)
+    FWD_CASE(11, 3) FWD_CASE(11, 4) FWD_CASE(11, 5)
+    FWD_CASE(12, 3) FWD_CASE(12, 4) FWD_CASE(12, 5)
+    FWD_CASE(13, 3) FWD_CASE(13, 4) FWD_CASE(13, 5)
+    FWD_CASE(14, 4) FWD_CASE(14, 5)
+    return set_error(BFHE_EINVAL, "no NTT configuration for this ring degree");
+}
+
+int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
+                   cudaStream_t st) {
+    if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
+    int log_m, log_e;
+    ntt_config((int)ctx->logN, &log_m, &log_e);
+    NttArgs a = make_args(ctx, io, n_limbs, map, mont);
+    const int blocks = n_polys * n_limbs;
+    const int subs = (int)(ctx->N >> log_m);
+    const bool full = subs == 1;
+    if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
+    int rc = [&]() -> int {
+        INV_CASE(10, 3) INV_CASE(10, 4) INV_CASE(10, 5)
+        INV_CASE(11, 3) INV_CASE(11, 4) INV_CASE(11, 5)
+        INV_CASE(12, 3) INV_CASE(12, 4) INV_CASE(12, 5)
+        INV_CASE(13, 3) INV_CASE(13, 4) INV_CASE(13, 5)
+        INV_CASE(14, 4) INV_CASE(14, 5)
+        return set_error(BFHE_EINVAL, "no NTT configuration for this ring degree");
+    }();
+    if (rc != BFHE_OK || full) return rc;
+    k_ntt_inv_top<<<dim3(blocks, 8), 256, 0, st>>>(a);
+    BFHE_LAUNCH_CHECK("k_ntt_inv_top");
+    return BFHE_OK;
+}

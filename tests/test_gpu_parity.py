@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA library against the oracle, bit for bit, through the C ABI.
+
+Every compared output is an integer array (RNS residues, slot values, key
+coefficients), so the bar is exact equality.  Inputs are seeded; ciphertext
+inputs are made by the oracle and uploaded, so each operation is checked on
+its own; encryption and key generation are compared separately.
+"""
+
+import random
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bfv, bridge
+from oracle.params import Params
+from paper_2204_12201_gb300 import inputs
+from tests.gpu_util import assert_ct_equal, ct_to_rns, cts_to_device, need_gpu, poly_to_rns
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(N=4096, L=2, alpha=1)            # the small workload's parameters
+SMALL = dict(N=1024, L=3, alpha=1)         # odd limb count, ragged vs. template sizes
+ALPHA2 = dict(N=1024, L=4, alpha=2)        # two special primes (mod-down by a 2-prime CRT)
+WIDE = dict(N=32768, L=2, alpha=2)         # N = 32768: the two-pass NTT path
+LOW_T = dict(N=1024, L=2, alpha=1, t=12289)  # t - 1 = 3 * 2^12: pow with an odd step
+
+
+class Pair:
+    """A GPU context and the oracle for the same parameters and key seed."""
+
+    def __init__(self, cfg, seed=1):
+        from paper_2204_12201_gb300 import bfhe
+        need_gpu()
+        self.bfhe = bfhe
+        self.prm = Params(**cfg)
+        kw = dict(cfg)
+        self.ctx = bfhe.Context(**kw)
+        self.ctx.keygen(seed)
+        self.keys = bfv.keygen(self.prm, seed)
+
+    def enc(self, vals, seed, idx):
+        return bfv.encrypt(self.prm, self.keys, [int(v) for v in vals], seed, idx)
+
+
+_pairs = {}
+
+
+def pair(name, cfg):
+    if name not in _pairs:
+        _pairs[name] = Pair(cfg)
+    return _pairs[name]
+
+
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("ALPHA2", ALPHA2), ("WIDE", WIDE),
+                                      ("LOW_T", LOW_T)])
+def test_params_and_keys(name, cfg):
+    P = pair(name, cfg)
+    prm = P.prm
+    assert P.ctx.primes == prm.q + prm.p + prm.b and P.ctx.K == prm.K
+    sk, pk, rlk = P.ctx.export_keys()
+    torch.cuda.synchronize()
+    assert sk.cpu().numpy().tolist() == P.keys.s
+    assert np.array_equal(pk.cpu().numpy(), ct_to_rns(prm, (P.keys.pk0, P.keys.pk1)))
+    qp = prm.q + prm.p
+    want = np.array([[poly_to_rns(bj, qp), poly_to_rns(aj, qp)] for bj, aj in P.keys.rlk])
+    assert np.array_equal(rlk.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("WIDE", WIDE)])
+def test_ntt_convolution(name, cfg):
+    """INTT(NTT(a) . NTT(b)) equals the exact negacyclic product mod q; INTT(NTT(a)) = a."""
+    from oracle.poly import negacyclic
+    P = pair(name, cfg)
+    prm = P.prm
+    N, L = prm.N, prm.L
+    rng = random.Random(5)
+    a = [[rng.randrange(q) for _ in range(N)] for q in prm.q]
+    b = [[rng.randrange(q) for _ in range(N)] for q in prm.q]
+    da = torch.tensor([a], dtype=torch.int64).cuda()
+    db = torch.tensor([b], dtype=torch.int64).cuda()
+    P.ctx.ntt(da)
+    P.ctx.ntt(db)
+    fa, fb = da.cpu().numpy(), db.cpu().numpy()
+    prod = np.array([[[int(x) * int(y) % q for x, y in zip(fa[0, i], fb[0, i])] for i, q in enumerate(prm.q)]],
+                    dtype=np.int64)
+    dp = torch.from_numpy(prod).cuda()
+    P.ctx.ntt(dp, inverse=True)
+    got = dp.cpu().numpy()[0]
+    for i, q in enumerate(prm.q):
+        assert np.array_equal(got[i], np.array([x % q for x in negacyclic(a[i], b[i])], dtype=np.int64))
+    P.ctx.ntt(da, inverse=True)
+    assert np.array_equal(da.cpu().numpy()[0], np.array(a, dtype=np.int64))
+
+
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("WIDE", WIDE)])
+def test_encrypt_decrypt(name, cfg):
+    P = pair(name, cfg)
+    prm = P.prm
+    y = inputs.slots(11, 3, prm.N, hi=prm.t)
+    ct = P.ctx.encrypt(torch.from_numpy(y).cuda(), seed=21)
+    want = [P.enc(y[i], 21, i) for i in range(3)]
+    assert_ct_equal(prm, ct, want, "encrypt")
+    # decrypt of the oracle's ciphertexts, and of the GPU's own
+    dec = P.ctx.decrypt(cts_to_device(prm, want)).cpu().numpy()
+    assert np.array_equal(dec, y)
+    assert np.array_equal(P.ctx.decrypt(ct).cpu().numpy(), y)
+
+
+def test_linear_ops():
+    P = pair("C1", C1)
+    prm, ctx = P.prm, P.ctx
+    t = prm.t
+    y = inputs.slots(12, 3, prm.N, hi=t)
+    a = [P.enc(y[0], 31, 0)]
+    b = [P.enc(y[1], 31, 1)]
+    da, db = cts_to_device(prm, a), cts_to_device(prm, b)
+    assert_ct_equal(prm, ctx.add(da, db), [bfv.add(prm, a[0], b[0])], "add")
+    assert_ct_equal(prm, ctx.sub(da, db), [bfv.sub(prm, a[0], b[0])], "sub")
+    assert_ct_equal(prm, ctx.add_const(da, 7), [bfv.add_const(prm, a[0], 7)], "add_const")
+    assert_ct_equal(prm, ctx.sub_const(da, t - 1), [bfv.sub_const(prm, a[0], t - 1)], "sub_const")
+    assert_ct_equal(prm, ctx.const_sub(1, da), [bfv.const_sub(prm, 1, a[0])], "const_sub")
+    assert_ct_equal(prm, ctx.mul_scalar(da, 65536), [bfv.mul_scalar(prm, a[0], 65536)], "mul_scalar")
+    w = y[2]
+    got = ctx.mul_plain(da, torch.from_numpy(w[None]).cuda())
+    assert_ct_equal(prm, got, [bfv.mul_plain(prm, a[0], [int(v) for v in w])], "mul_plain")
+    # in-place add (out aliases a)
+    ctx.add(da, db, out=da)
+    assert_ct_equal(prm, da, [bfv.add(prm, a[0], b[0])], "add in place")
+
+
+@pytest.mark.parametrize("name,cfg,n", [("C1", C1, 3), ("SMALL", SMALL, 2), ("ALPHA2", ALPHA2, 2),
+                                        ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2)])
+def test_mul_relin(name, cfg, n):
+    P = pair(name, cfg)
+    prm = P.prm
+    y = inputs.slots(13, 2 * n, prm.N, hi=prm.t)
+    a = [P.enc(y[i], 41, i) for i in range(n)]
+    b = [P.enc(y[n + i], 41, n + i) for i in range(n)]
+    got = P.ctx.mul_relin(cts_to_device(prm, a), cts_to_device(prm, b))
+    want = [bfv.mul_relin(prm, P.keys, a[i], b[i]) for i in range(n)]
+    assert_ct_equal(prm, got, want, "mul_relin")
+    dec = P.ctx.decrypt(got).cpu().numpy()
+    assert np.array_equal(dec, (y[:n] * y[n:]) % prm.t)
+
+
+def test_mul_relin_edge_values():
+    """Coefficients at the centring boundary (Q-1)/2, (Q+1)/2, 0 and Q-1 and a zero ciphertext."""
+    P = pair("SMALL", SMALL)
+    prm = P.prm
+    Q = prm.Q
+    a = P.enc(inputs.slots(14, 1, prm.N, hi=prm.t)[0], 51, 0)
+    b = P.enc(inputs.slots(15, 1, prm.N, hi=prm.t)[0], 51, 1)
+    special = [(Q - 1) // 2, (Q + 1) // 2, 0, Q - 1, 1]
+    a = ([special[k % 5] if k < 10 else x for k, x in enumerate(a[0])], a[1])
+    b = (b[0], [special[(k + 2) % 5] if k < 10 else x for k, x in enumerate(b[1])])
+    zero = ([0] * prm.N, [0] * prm.N)
+    got = P.ctx.mul_relin(cts_to_device(prm, [a, zero]), cts_to_device(prm, [b, b]))
+    assert_ct_equal(prm, got, [bfv.mul_relin(prm, P.keys, a, b), zero], "mul_relin edges")
+
+
+def test_gates_and_counts():
+    P = pair("SMALL", SMALL)
+    prm, ctx = P.prm, P.ctx
+    rng = np.random.default_rng(3)
+    bits = rng.integers(0, 2, size=(3, prm.N))
+    cts = [P.enc(bits[i], 61, i) for i in range(3)]
+    x, y, z = (cts_to_device(prm, [c]) for c in cts)
+    for g in range(8):
+        ev = bridge.Evaluator(prm, P.keys)
+        want = ev.gate(g, *cts)
+        ctx.op_counts(reset=True)
+        got = ctx.bit_gate(g, x, y, z)
+        assert_ct_equal(prm, got, [want], "gate %s" % bridge.GATE_NAMES[g])
+        assert ctx.op_counts()[:3] == ev.counts(), bridge.GATE_NAMES[g]
+
+
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_bits_to_mod(s):
+    P = pair("C1", C1)
+    prm = P.prm
+    vals = inputs.slots(16, 1, prm.N, hi=1 << s)[0]
+    planes = inputs.bit_planes(vals, s)
+    bits = [P.enc(planes[k], 71, k) for k in range(s)]
+    dev = torch.from_numpy(np.stack([ct_to_rns(prm, c)[None] for c in bits])).cuda()   # [s][1][2][L][N]
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.bits_to_mod(bits)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.bits_to_mod(dev)
+    assert_ct_equal(prm, got, [want], "bits_to_mod")
+    assert P.ctx.op_counts()[:3] == ev.counts()
+    assert np.array_equal(P.ctx.decrypt(got).cpu().numpy()[0], vals)
+
+
+@pytest.mark.parametrize("e", [2, 3, 12288])
+def test_pow(e):
+    P = pair("LOW_T", LOW_T)
+    prm = P.prm
+    x = P.enc(inputs.slots(17, 1, prm.N, hi=prm.t)[0], 81, 0)
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.pow(x, e)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.pow(cts_to_device(prm, [x]), e)
+    assert_ct_equal(prm, got, [want], "pow %d" % e)
+    assert P.ctx.op_counts()[2] == ev.n_mul == bridge.pow_mul_count(e)
+
+
+@pytest.mark.parametrize("mode", [bridge.PAPER, bridge.SELECT])
+def test_mod_to_bits(mode):
+    P = pair("LOW_T", LOW_T)
+    prm = P.prm
+    s, cands = 2, range(0, 4)
+    xs = inputs.slots(18, 1, prm.N, hi=4)[0]
+    x = P.enc(xs, 91, 0)
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.mod_to_bits(x, s, cands, mode)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.mod_to_bits(cts_to_device(prm, [x]), s, cands[0], cands[-1], mode)
+    for k in range(s):
+        assert_ct_equal(prm, got[k], [want[k]], "mod_to_bits bit %d" % k)
+    assert P.ctx.op_counts()[:3] == ev.counts()
+
+
+def test_gate_level_matches_gates():
+    """One level with every gate type (multiplying gates first, NOT last) on a shared wire array."""
+    P = pair("SMALL", SMALL)
+    prm, ctx = P.prm, P.ctx
+    rng = np.random.default_rng(4)
+    bits = rng.integers(0, 2, size=(3, prm.N))
+    cts = [P.enc(bits[i], 101, i) for i in range(3)]
+    gates = [0, 1, 2, 3, 4, 5, 7, 6]                       # NOT (6) last
+    n_w = 3 + len(gates)
+    wires = torch.zeros(n_w, 1, 2, prm.L, prm.N, dtype=torch.int64, device="cuda")
+    wires[:3] = cts_to_device(prm, cts)[:, None]
+    table = torch.tensor([[g, 0, 1, 2, 3 + i] for i, g in enumerate(gates)], dtype=torch.int32, device="cuda")
+    ctx.gate_level(wires, table, len(gates), len(gates) - 1)
+    for i, g in enumerate(gates):
+        want = bridge.Evaluator(prm, P.keys).gate(g, *cts)
+        assert_ct_equal(prm, wires[3 + i], [want], "level gate %s" % bridge.GATE_NAMES[g])
