@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the bridged-FHE hot path on GB300: one JSON line on rank 0.
+
+A step is one pass of the whole hot path over one batch: the genotype-shaped
+job at N = 16384 (8 data primes of 50 bits + 1 special, t = 65537):
+encrypt 32 tag-genotype slot vectors (2000 targets x 8 individuals packed in
+16000 of the 16384 slots), SecureMod dot products with 6-bit public weights
+for 3 classes (mul_plain + adds), the bridge SecureMod -> SecureUint<12>
+(Eq. 2 / Listings 7-8, paper mode: every candidate c in 0..4095 runs 16
+chained squarings and 12 ANDs), a levelised 3-way argmax circuit over the
+bits, and decryption of the two index bits.  The metric counts the
+relinearised ciphertext multiplies the step performs (op counter) per
+second.  Extra keys report the batched-vs-per-op mul_relin rate at
+N = 16384, bit-gates/s of the 16-bit comparator and 16x16 multiplier
+circuits at N = 8192 (eager and CUDA-graph), and the modmul probe.
+
+--impl reference times the CPU oracle (the plain arbitrary-precision BFV the
+library is checked against) on the host cores instead.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "mul_relin/sec at N=16384 and bit-gates/sec, batched vs per-op, bit-exact; % roofline"
+UNIT = "mul_relin/s"
+WL = dict(N=16384, L=8, alpha=1, t=65537)
+N_IND, N_TARGETS, N_TAGS, N_CLASSES, S_BITS = 8, 2000, 32, 3, 12
+WORKLOAD = ("genotype-shaped job: BFV N=16384, 8x50-bit data primes + 1 special, t=65537; "
+            "2000 targets x 8 individuals slot-packed, 32 tag ciphertexts, 3-class 6-bit-weight "
+            "SecureMod dot products, mod_to_bits s=12 over c in 0..4095 (paper mode), 3-way argmax "
+            "circuit, decrypt")
+CPU_SAMPLE_N = 16384
+
+
+# --------------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_modmul_per_s(sms, mhz):
+    """Derived integer-pipe peak: 64 32-bit IMAD issue slots per SM per clock; one 64-bit
+    Shoup product takes 16 slots (four 32x32->64 wide products of the high half at 2 slots,
+    and one wide + two narrow products for each of the two low halves)."""
+    return sms * 64.0 * mhz * 1e6 / 16.0
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def genotype_inputs(seed):
+    from paper_2204_12201_gb300 import inputs
+    N = WL["N"]
+    used = N_IND * N_TARGETS
+    G = inputs.genotypes(seed, N_IND, N_TARGETS, N_TAGS)                 # [32][16000]
+    W = inputs.weights(seed + 1, N_CLASSES, N_TAGS, N_TARGETS, N_IND)     # [3][32][16000]
+    import numpy as np
+    Gs = np.zeros((N_TAGS, N), dtype=np.int64)
+    Ws = np.zeros((N_CLASSES, N_TAGS, N), dtype=np.int64)
+    Gs[:, :used] = G
+    Ws[:, :, :used] = W
+    return Gs, Ws
+
+
+# --------------------------------------------------------------------------- the job
+class GenotypeJob:
+    def __init__(self, ctx, use_graph=False):
+        import torch
+        from paper_2204_12201_gb300 import circuits
+        self.torch = torch
+        self.ctx = ctx
+        net = circuits.Netlist()
+        s0, s1, s2 = net.inputs(S_BITS), net.inputs(S_BITS), net.inputs(S_BITS)
+        self.out_wires = net.argmax3(s0, s1, s2)
+        self.circ = circuits.Compiled(ctx, net, 1)
+        self.circuit_muls = net.n_mul
+
+    def run(self, G_dev, W_dev, seed):
+        torch, ctx = self.torch, self.ctx
+        N, L = ctx.N, ctx.L
+        g = ctx.encrypt(G_dev, seed)                                  # [32] tag ciphertexts
+        rep = g.repeat(N_CLASSES, 1, 1, 1)                            # [96]
+        x = ctx.mul_plain(rep, W_dev.view(N_CLASSES * N_TAGS, N))     # weighted tags
+        x = x.view(N_CLASSES, N_TAGS, 2, L, N)
+        while x.shape[1] > 1:                                         # sum over tags
+            h = x.shape[1] // 2
+            x = ctx.add(x[:, :h].contiguous(), x[:, h:].contiguous())
+        scores = x.view(N_CLASSES, 2, L, N)                           # SecureMod scores < 4096
+        bits = ctx.mod_to_bits(scores, S_BITS, 0, (1 << S_BITS) - 1)  # [12][3]
+        self.circ.set_inputs(bits.transpose(0, 1).reshape(N_CLASSES * S_BITS, 1, 2, L, N))
+        self.circ.run()
+        idx = self.circ.out(self.out_wires).view(2, 2, L, N)
+        return ctx.decrypt(idx)                                       # [2][N]: index bits per slot
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def _oracle_mul_relin(args):
+    """One oracle mul_relin on random ciphertexts and a random-key stand-in; returns seconds."""
+    N, L, alpha, seed = args
+    import random
+    sys.path.insert(0, ROOT)
+    from oracle import bfv
+    from oracle.params import Params
+    prm = Params(N=N, L=L, alpha=alpha)
+    rng = random.Random(seed)
+    Q, PQ = prm.Q, prm.P * prm.Q
+    ct = lambda: ([rng.randrange(Q) for _ in range(N)], [rng.randrange(Q) for _ in range(N)])
+    a, b = ct(), ct()
+    rlk = [([rng.randrange(PQ) for _ in range(N)], [rng.randrange(PQ) for _ in range(N)]) for _ in range(L)]
+    keys = bfv.Keys([0] * N, None, None, rlk)
+    t0 = time.perf_counter()
+    bfv.mul_relin(prm, keys, a, b)
+    return time.perf_counter() - t0
+
+
+def cpu_pool_start(n_procs, N=CPU_SAMPLE_N):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(n_procs)
+    res = pool.map_async(_oracle_mul_relin, [(N, WL["L"], WL["alpha"], 100 + i) for i in range(n_procs)])
+    return pool, res
+
+
+def cpu_pool_finish(pool, res, n_procs, wall0):
+    times = res.get()
+    wall = time.perf_counter() - wall0
+    pool.close()
+    pool.join()
+    return {"value": n_procs / max(times), "unit": UNIT, "cores": n_procs, "kind": "oracle",
+            "sample": "%d oracle mul_relin at N=16384, L=8, alpha=1 (random ciphertexts, random-key "
+                      "stand-in), one per process in parallel; rate = count / slowest process" % n_procs,
+            "per_op_s": round(statistics.mean(times), 2), "wall_s": round(wall, 1)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_procs = max(1, min(16, host_cores()))
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(n_procs)
+    for w in range(args.warmup):   # untimed: module import and a small op per process
+        pool.map(_oracle_mul_relin, [(1024, 2, 1, 900 + w * 100 + i) for i in range(n_procs)])
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        pool.map(_oracle_mul_relin, [(CPU_SAMPLE_N, WL["L"], WL["alpha"], s * 100 + i) for i in range(n_procs)])
+        done += n_procs
+    el = time.perf_counter() - t0
+    pool.close()
+    pool.join()
+    v = done / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (exact)",
+            "data": "synthetic",
+            "config": {"workload": "oracle mul_relin at N=16384, L=8, alpha=1 (one per host core per step)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_procs, "kind": "oracle",
+                             "sample": "%d mul_relin per step, one per process" % n_procs},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- extras
+def extras(torch, bfhe, circuits, ctx16):
+    out = {}
+    N = ctx16.N
+    # batched vs per-op mul_relin at N = 16384
+    B = 64
+    a = ctx16.encrypt(torch.randint(0, 65537, (B, N), dtype=torch.int64, device="cuda"), 7)
+    b = ctx16.encrypt(torch.randint(0, 65537, (B, N), dtype=torch.int64, device="cuda"), 8)
+    o = torch.empty_like(a)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_b = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
+    ms_p = timed(lambda: [ctx16.mul_relin(a[i:i + 1], b[i:i + 1], out=o[i:i + 1]) for i in range(B)], 3)
+    out["mul_relin_batched_per_s"] = B / ms_b * 1e3
+    out["mul_relin_per_op_per_s"] = B / ms_p * 1e3
+    # graph-captured per-op sequence
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for i in range(B):
+                ctx16.mul_relin(a[i:i + 1], b[i:i + 1], out=o[i:i + 1])
+    torch.cuda.current_stream().wait_stream(s)
+    ms_g = timed(g.replay, 3)
+    out["mul_relin_per_op_graph_per_s"] = B / ms_g * 1e3
+    del g
+    # bit-level circuits at N = 8192, L = 4
+    ctx8 = bfhe.Context(N=8192, L=4, alpha=1)
+    ctx8.keygen(3)
+    rng = torch.Generator().manual_seed(5)
+    for name, build in (("lt16", lambda n: [n.less_than(n.inputs(16), n.inputs(16))]),
+                        ("mul16", lambda n: n.multiply(n.inputs(16), n.inputs(16)))):
+        net = circuits.Netlist()
+        build(net)
+        comp = circuits.Compiled(ctx8, net, 1)
+        ops = torch.randint(0, 2, (net.n_inputs, 8192), generator=rng, dtype=torch.int64).cuda()
+        comp.set_inputs(ctx8.encrypt(ops, 9).view(net.n_inputs, 1, 2, 4, 8192))
+        ms_e = timed(comp.run, 2)
+        comp.capture()
+        ms_gr = timed(comp.replay, 3)
+        out["bit_gates_per_s_%s_eager" % name] = net.n_mul / ms_e * 1e3
+        out["bit_gates_per_s_%s_graph" % name] = net.n_mul / ms_gr * 1e3
+        out["%s_gates" % name] = net.n_mul
+        del comp
+    ctx8.close()
+    out["modmul_probe_per_s"] = bfhe.probe_modmul(torch.cuda.current_device())
+    return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
+
+
+# --------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU leg")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    args.warmup = max(3, args.warmup)
+
+    # the oracle leg starts first (spawned processes, before any GPU call) and runs on the host
+    # cores while the GPU sets up and warms up; it is collected before the timed region
+    cpu = None
+    n_cpu = 0
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_cpu = max(1, min(16, host_cores() - 2))
+        wall0 = time.perf_counter()
+        cpu = cpu_pool_start(n_cpu) + (wall0,)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_12201_gb300 import bfhe, circuits
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ctx = bfhe.Context(N=WL["N"], L=WL["L"], alpha=WL["alpha"], t=WL["t"], device=local)
+    ctx.keygen(1 + rank)
+    job = GenotypeJob(ctx)
+    Gs, Ws = genotype_inputs(1004 + rank)
+    G_dev = torch.from_numpy(Gs).cuda()
+    W_dev = torch.from_numpy(Ws).cuda()
+    for w in range(args.warmup):
+        job.run(G_dev, W_dev, seed=10 + w)
+    torch.cuda.synchronize()
+    cpu_line = None
+    if cpu is not None:
+        cpu_line = cpu_pool_finish(cpu[0], cpu[1], n_cpu, cpu[2])
+
+    # ---------------- timed region: K steps, inputs resident in HBM
+    ctx.op_counts(reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = bfhe.launch_count()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(args.steps):
+        res = job.run(G_dev, W_dev, seed=100 + s)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = bfhe.launch_count() - launches0
+    clk = clocks.stop()
+    n_add, n_sub, n_mul, n_pmul = ctx.op_counts(reset=True)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = n_mul * world / (ms / 1e3)
+
+    # ---------------- e2e: the same job from host buffers (pinned), copies inside the timed region
+    G_h = torch.from_numpy(Gs).pin_memory()
+    W_h = torch.from_numpy(Ws).pin_memory()
+    out_h = torch.empty((2, WL["N"]), dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    ctx.op_counts(reset=True)
+    t0 = time.perf_counter()
+    g_d = G_h.to("cuda", non_blocking=True)
+    w_d = W_h.to("cuda", non_blocking=True)
+    r = job.run(g_d, w_d, seed=500)
+    out_h.copy_(r, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_mul = ctx.op_counts(reset=True)[2]
+    e2e = {"value": e2e_mul / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Gs.nbytes + Ws.nbytes),
+           "d2h_bytes_per_step": int(out_h.numel() * 8)}
+
+    # ---------------- roofline of the dominant kernel class
+    peaks, src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    peak = alu_peak_modmul_per_s(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
+    dom = max(prof, key=lambda k: prof[k][0])
+    d_ms, d_launch, d_work = prof[dom]
+    achieved = d_work / (d_ms / 1e3)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "modmul/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: %d SMs x 64 IMAD/clk x %.0f MHz / 16 IMAD slots per 64-bit "
+                               "Shoup product (clock from MEASURED_PEAKS.json, %s)"
+                               % (props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0), src),
+                "avg_launch_ms": d_ms / max(1, d_launch), "launches": d_launch,
+                "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 3)
+                                 for k, v in prof.items()}}
+
+    ext = {} if args.no_extras else extras(torch, bfhe, circuits, ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": WL["N"], "L": WL["L"], "alpha": WL["alpha"],
+                           "t": WL["t"], "mul_relin_per_step": n_mul // args.steps,
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "no flush: per-step working set > 10 GB >> 129 MB L2"},
+                "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu_line, "ops_per_step": {"add": n_add // args.steps, "sub": n_sub // args.steps,
+                                                            "mul": n_mul // args.steps, "plain_mul": n_pmul // args.steps},
+                "extras": ext}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

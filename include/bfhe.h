@@ -134,14 +134,20 @@ enum { BFHE_AND = 0, BFHE_OR = 1, BFHE_XOR = 2, BFHE_NAND = 3, BFHE_NOR = 4, BFH
 int bfhe_bit_gate(bfhe_ctx* ctx, int gate, const uint64_t* x, const uint64_t* y, const uint64_t* z,
                   uint64_t* out, size_t n, void* stream);
 
-/* A levelised gate list over one wire array: all gates of one circuit depth
- * level share one batched multiply.  wires: uint64 [n_wires][n][2][L][N]
- * (n slot-packed ciphertexts per wire); table: DEVICE int32 [n_gates][5] =
- * (gate, x, y, z, out) wire indices (unused inputs ignored), the n_mul gates
- * with a multiply first and the NOT gates after them.  No gate may read a
- * wire that another gate of the same call writes.  Counts only the
- * multiplies (the table stays on the device).  Capturable in a CUDA graph
- * once scratch is reserved. */
+/* A levelised gate list over one wire array: all multiplying entries of one
+ * circuit depth level share one batched multiply.  wires: uint64
+ * [n_wires][n][2][L][N] (n slot-packed ciphertexts per wire); table: DEVICE
+ * int32 [n_gates][5] = (op, x, y, z, out) wire indices, the n_mul entries
+ * with a multiply first.  op is a gate above (BFHE_AND .. BFHE_MUX, with the
+ * Sec. 3.1 equation), BFHE_OP_MUL (out = x * y, relinearised) or
+ * BFHE_OP_LIN | code << 8, a linear node out = cc Delta + cx x + cy y + cz z
+ * with code = ((cc+2) 5 + (cx+2)) 25 + (cy+2) 5 + (cz+2), coefficients in
+ * -2..2 (no multiply; place after the n_mul entries).  No entry may read a
+ * wire that another entry of the same call writes; wire indices must be
+ * < n_wires (not checked on the device).  Counts only the multiplies.
+ * Needs no host synchronisation: capturable in a CUDA graph once scratch is
+ * reserved (bfhe_reserve) and one call of the same shape has run. */
+enum { BFHE_OP_MUL = 8, BFHE_OP_LIN = 9 };
 int bfhe_gate_level(bfhe_ctx* ctx, uint64_t* wires, size_t n_wires, size_t n, const int32_t* table,
                     size_t n_gates, size_t n_mul, void* stream);
 
@@ -179,6 +185,29 @@ int bfhe_op_counts(bfhe_ctx* ctx, uint64_t out[4], int reset);
  * (n_limbs <= L); forward maps coefficients to the library's internal
  * evaluation order, inverse maps back (inputs canonical). */
 int bfhe_ntt(bfhe_ctx* ctx, uint64_t* data, size_t n_polys, uint32_t n_limbs, int inverse, void* stream);
+
+/* Measurement support.  While profiling is on, every launch of the kernel
+ * classes below is bracketed by CUDA events on its own stream;
+ * bfhe_profile_read synchronises on the last event and returns, per class,
+ * the summed device time in ms, the number of launches and (work_out, may
+ * be NULL) the algorithmic 64-bit modular multiplies those launches
+ * performed (arrays of BFHE_K_COUNT), then clears the record.  Modmul
+ * counts: NTT (N/2) log2 N per limb; modup per coefficient L(L-1)/2 +
+ * K(L-1); scale per coefficient of each of 3 polys 2L + 3K + L(L-1)/2 +
+ * K(L-1) + K(K-1)/2 + L(K-1); tensor 4 per limb word; inner 2L per word of
+ * the Q u P limbs; moddown per coefficient alpha(alpha-1)/2 + L alpha. */
+enum { BFHE_K_NTT_FWD = 0, BFHE_K_NTT_INV = 1, BFHE_K_MODUP = 2, BFHE_K_TENSOR = 3, BFHE_K_SCALE = 4,
+       BFHE_K_INNER = 5, BFHE_K_MODDOWN = 6, BFHE_K_COUNT = 7 };
+int bfhe_profile(bfhe_ctx* ctx, int enable);
+int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out);
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t bfhe_launch_count(void);
+
+/* Integer-pipe probe: a kernel of independent 64-bit Shoup modular-multiply
+ * chains on every SM (grid = SMs x 4 CTAs of 256 threads, 8 chains per
+ * thread, `iters` steps each).  *modmul_per_s = modmuls / device time. */
+int bfhe_probe_modmul(int device, uint32_t iters, double* modmul_per_s, void* stream);
 
 /* Message of the last failed call on this thread (static storage). */
 const char* bfhe_strerror(int code);

@@ -16,7 +16,9 @@ import torch
 from .build import lib_path
 
 AND, OR, XOR, NAND, NOR, XNOR, NOT, MUX = range(8)
+OP_MUL, OP_LIN = 8, 9
 PAPER, SELECT = 0, 1
+KERNEL_CLASSES = ("ntt_fwd", "ntt_inv", "modup", "tensor", "scale", "inner", "moddown")
 
 _lib = None
 
@@ -59,6 +61,10 @@ def load():
         "bfhe_pow": (I, [P, P, U64, P, S, P]),
         "bfhe_op_counts": (I, [P, P, I]),
         "bfhe_ntt": (I, [P, P, S, U32, I, P]),
+        "bfhe_profile": (I, [P, I]),
+        "bfhe_profile_read": (I, [P, P, P, P]),
+        "bfhe_probe_modmul": (I, [I, U32, P, P]),
+        "bfhe_launch_count": (ctypes.c_uint64, []),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
         "bfhe_last_error": (ctypes.c_char_p, []),
     }
@@ -233,3 +239,28 @@ class Context:
         n_polys = data.numel() // (n_limbs * self.N)
         _check(self.lib.bfhe_ntt(self.h, _ptr(data), n_polys, n_limbs, int(inverse), self.stream))
         return data
+
+    def profile(self, enable):
+        _check(self.lib.bfhe_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        """{class: (ms, launches, modmuls)} since the last read (synchronises)."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        cnt = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
+        work = (ctypes.c_double * len(KERNEL_CLASSES))()
+        _check(self.lib.bfhe_profile_read(self.h, ms, cnt, work))
+        return {k: (ms[i], int(cnt[i]), work[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def probe_modmul(device=0, iters=1 << 14):
+    """Measured 64-bit Shoup modmul rate of this GPU (modmul/s)."""
+    lib = load()
+    out = ctypes.c_double()
+    _check(lib.bfhe_probe_modmul(device, iters, ctypes.byref(out),
+                                 ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)))
+    return out.value
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(load().bfhe_launch_count())

@@ -535,3 +535,36 @@ extern "C" int bfhe_ntt(bfhe_ctx* c, uint64_t* data, size_t n_polys, uint32_t n_
     if (inverse) return launch_ntt_inv(c, io, (int)n_polys, (int)n_limbs, c->mapQ(), 0, S(stream));
     return launch_ntt_fwd(c, io, (int)n_polys, (int)n_limbs, c->mapQ(), S(stream));
 }
+
+extern "C" int bfhe_probe_modmul(int device, uint32_t iters, double* modmul_per_s, void* stream) {
+    if (!modmul_per_s || iters == 0) return set_error(BFHE_EINVAL, "bad arguments");
+    BFHE_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    BFHE_CUDA(cudaGetDeviceProperties(&prop, device));
+    const int threads = 256, blocks = prop.multiProcessorCount * 4;
+    u64* buf = nullptr;
+    BFHE_CUDA(cudaMalloc(&buf, (size_t)blocks * threads * sizeof(u64)));
+    const u64 q = 1125899906826241ull;   // a 50-bit prime = 1 mod 2^16
+    const u64 w = 123456789012345ull % q, ws = (u64)(((u128)w << 64) / q);
+    cudaStream_t st = S(stream);
+    cudaEvent_t e0, e1;
+    BFHE_CUDA(cudaEventCreate(&e0));
+    BFHE_CUDA(cudaEventCreate(&e1));
+    int rc = launch_probe_modmul(buf, blocks, threads, iters / 8 + 1, q, w, ws, st);   // warm-up
+    if (rc == BFHE_OK) {
+        cudaEventRecord(e0, st);
+        rc = launch_probe_modmul(buf, blocks, threads, iters, q, w, ws, st);
+        cudaEventRecord(e1, st);
+    }
+    float ms = 0;
+    if (rc == BFHE_OK) {
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_check(e, "probe events");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc == BFHE_OK) *modmul_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
+    return rc;
+}

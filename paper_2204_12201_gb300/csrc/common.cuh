@@ -146,6 +146,16 @@ struct bfhe_ctx {
 
     uint64_t counts[4] = {0, 0, 0, 0};
 
+    // launch timing (measurement only): pending (class, start, stop) event triples
+    struct ProfRec {
+        int cls;
+        double work;
+        cudaEvent_t a, b;
+    };
+    mutable bool prof_on = false;
+    mutable std::vector<ProfRec> prof_pending;
+    mutable std::vector<cudaEvent_t> prof_pool;
+
     LimbMap mapQ() const { return LimbMap{(int)L, 0}; }
     LimbMap mapQP() const { return LimbMap{(int)(L + alpha), 0}; }
     LimbMap mapQB() const { return LimbMap{(int)L, (int)alpha}; }
@@ -155,6 +165,8 @@ struct bfhe_ctx {
 
 // ------------------------------------------------------------------ host helpers (host.cu)
 int set_error(int code, const std::string& msg);
+// process-wide count of kernel launches made by this library (measurement)
+void count_launch();
 int cuda_check(cudaError_t e, const char* where);
 #define BFHE_CUDA(call)                                          \
     do {                                                         \
@@ -163,6 +175,7 @@ int cuda_check(cudaError_t e, const char* where);
     } while (0)
 #define BFHE_LAUNCH_CHECK(where)                                 \
     do {                                                         \
+        count_launch();                                          \
         cudaError_t _e = cudaGetLastError();                     \
         if (_e != cudaSuccess) return cuda_check(_e, where);     \
     } while (0)
@@ -171,6 +184,18 @@ int cuda_check(cudaError_t e, const char* where);
 int ctx_scratch(bfhe_ctx* ctx, size_t bytes, void** out);
 // bytes of scratch one mul_relin of n ciphertexts needs
 size_t mul_scratch_bytes(const bfhe_ctx* ctx, size_t n);
+
+// RAII bracket of one launcher's kernels by CUDA events when profiling is on
+// (work = the launch's algorithmic 64-bit modular multiplies)
+struct ProfScope {
+    const bfhe_ctx* c;
+    int cls;
+    double work;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w);
+    ~ProfScope();
+};
 
 // ------------------------------------------------------------------ kernel launchers (ntt.cu)
 // In/out-of-place negacyclic NTT over n_polys x n_limbs limbs.

@@ -10,6 +10,7 @@
 // of t (the encode/decode NTT uses psi = zeta, so slot j = m(zeta^(2j+1))).
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -17,6 +18,7 @@
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
 
 u64 mulmod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
 
@@ -201,6 +203,10 @@ std::vector<u64> pair_table(const std::vector<u64>& w, const std::vector<u64>& q
 
 }  // namespace
 
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" uint64_t bfhe_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 // ------------------------------------------------------------------ errors
 int set_error(int code, const std::string& msg) {
     g_last_error = msg;
@@ -224,6 +230,62 @@ extern "C" const char* bfhe_strerror(int code) {
         case BFHE_ESTATE: return "call out of order";
         default: return "unknown error";
     }
+}
+
+// ------------------------------------------------------------------ launch timing
+static cudaEvent_t take_event(const bfhe_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+ProfScope::ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w) : c(ctx), cls(k), work(w), st(s) {
+    if (!c->prof_on) return;
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+    if (!a || !b) return;
+    cudaEventRecord(b, st);
+    c->prof_pending.push_back(bfhe_ctx::ProfRec{cls, work, a, b});
+}
+
+extern "C" int bfhe_profile(bfhe_ctx* ctx, int enable) {
+    if (!ctx) return set_error(BFHE_EINVAL, "null context");
+    ctx->prof_on = enable != 0;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out) {
+    if (!ctx || !ms_out || !launches_out) return set_error(BFHE_EINVAL, "null argument");
+    for (int k = 0; k < BFHE_K_COUNT; ++k) {
+        ms_out[k] = 0;
+        launches_out[k] = 0;
+        if (work_out) work_out[k] = 0;
+    }
+    int rc = BFHE_OK;
+    for (auto& r : ctx->prof_pending) {
+        float ms = 0;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_check(e, "profile events");
+        if (r.cls >= 0 && r.cls < BFHE_K_COUNT) {
+            ms_out[r.cls] += ms;
+            launches_out[r.cls] += 1;
+            if (work_out) work_out[r.cls] += r.work;
+        }
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    return rc;
 }
 
 // ------------------------------------------------------------------ scratch
@@ -465,6 +527,11 @@ extern "C" void bfhe_ctx_destroy(bfhe_ctx* ctx) {
     cudaFree(ctx->d_pk);
     cudaFree(ctx->d_pk_ntt);
     cudaFree(ctx->d_rlk_ntt);
+    for (auto& r : ctx->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     delete ctx;
 }
 

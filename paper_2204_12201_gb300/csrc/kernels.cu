@@ -485,11 +485,11 @@ __global__ void k_gather_ops(u64* A, u64* B, const u64* wires, size_t ctw, const
         const u64 q = qtab[(o / N) % L];
         A[idx] = wires[(size_t)e[1] * ctw + o];
         const u64 yv = wires[(size_t)e[2] * ctw + o];
-        B[idx] = e[0] == BFHE_MUX ? sub_mod(yv, wires[(size_t)e[3] * ctw + o], q) : yv;
+        B[idx] = (e[0] & 0xff) == BFHE_MUX ? sub_mod(yv, wires[(size_t)e[3] * ctw + o], q) : yv;
     }
 }
 
-// gate epilogue: wires[out] = lin(gate)(x, y, z, prod[g]); gates g >= n_mul (NOT) have no product
+// gate epilogue: wires[out] = lin(op)(x, y, z, prod[g]); entries g >= n_mul have no product
 __global__ void k_gate_epilogue(u64* wires, size_t ctw, const int32_t* table, int n_gates, int n_mul,
                                 const u64* prod, int L, const u64* qtab, const u64* delta, int N) {
     const size_t total = (size_t)n_gates * ctw;
@@ -499,7 +499,27 @@ __global__ void k_gate_epilogue(u64* wires, size_t ctw, const int32_t* table, in
         const int g = (int)(idx / ctw);
         const size_t o = idx % ctw;
         const int32_t* e = table + 5 * g;
-        const int* cf = c_gate_coef[e[0] & 7];
+        const int op = e[0] & 0xff;
+        int cc, cx, cy, cz, cp;
+        if (op == BFHE_OP_MUL) {
+            cc = cx = cy = cz = 0;
+            cp = 1;
+        } else if (op == BFHE_OP_LIN) {
+            const int code = e[0] >> 8;
+            cc = code / 125 - 2;
+            cx = (code / 25) % 5 - 2;
+            cy = (code / 5) % 5 - 2;
+            cz = code % 5 - 2;
+            cp = 0;
+        } else {
+            const int* cf = c_gate_coef[op & 7];
+            cc = cf[0];
+            cx = cf[1];
+            cy = cf[2];
+            cz = cf[3];
+            cp = cf[4];
+        }
+        if (g >= n_mul) cp = 0;
         const int i = (int)((o / N) % L);
         const int k = (int)(o % N);
         const int comp = (int)((o / per_comp) & 1);
@@ -508,9 +528,23 @@ __global__ void k_gate_epilogue(u64* wires, size_t ctw, const int32_t* table, in
         const u64* z = wires + (size_t)e[3] * ctw;
         const u64* p = g < n_mul ? prod + (size_t)g * ctw : nullptr;
         wires[(size_t)e[4] * ctw + o] =
-            lin_word(cf[0], cf[1], cf[2], cf[3], g < n_mul ? cf[4] : 0, 1, x, y, z, p, o, comp, k, qtab[i],
-                     delta[i], delta[L + i]);
+            lin_word(cc, cx, cy, cz, cp, 1, x, y, z, p, o, comp, k, qtab[i], delta[i], delta[L + i]);
     }
+}
+
+// integer-pipe probe: 8 independent lazy Shoup chains per thread
+__global__ void k_probe_modmul(u64* out, uint32_t iters, u64 q, u64 w, u64 ws) {
+    u64 x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (u64)threadIdx.x * 977u + (u64)blockIdx.x * 131u + (u64)i;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = shoup_lazy(x[i], w, ws, q);
+    }
+    u64 s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s ^= x[i];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 // trivial ciphertexts (Delta bit_k(c_base + c), 0), layout [s][C][n][2][L][N]
@@ -612,12 +646,14 @@ int launch_pointwise(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* out, 
 }
 
 int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, cudaStream_t st) {
+    ProfScope ps(ctx, BFHE_K_TENSOR, st, 4.0 * n * (ctx->L + ctx->K) * ctx->N);
     const int LK = (int)(ctx->L + ctx->K);
     LAUNCH(k_tensor, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
     return BFHE_OK;
 }
 
 int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
+    ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
     const int QP = (int)(ctx->L + ctx->alpha);
     constexpr int CB = 4;
     const size_t work = (size_t)QP * ctx->N * ((n + CB - 1) / CB);
@@ -670,15 +706,22 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
     }
 
 int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, cudaStream_t st) {
+    const double L_ = ctx->L, K_ = ctx->K;
+    ProfScope ps(ctx, BFHE_K_MODUP, st, 4.0 * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
     SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, st)
 }
 
 int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
     if (ctx->K != ctx->L + 1) return set_error(BFHE_EINVAL, "auxiliary base must have L+1 primes");
+    const double L_ = ctx->L, K_ = ctx->K;
+    ProfScope ps(ctx, BFHE_K_SCALE, st,
+                 3.0 * n * ctx->N * (2 * L_ + 3 * K_ + L_ * (L_ - 1) / 2 + K_ * (L_ - 1) + K_ * (K_ - 1) / 2 + L_ * (K_ - 1)));
     SWITCH_L(ctx->L, run_scale, ctx, X, C3, n, st)
 }
 
 int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st) {
+    const double A_ = ctx->alpha;
+    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_));
     const size_t work = (size_t)n * 2 * ctx->N;
     if (ctx->alpha == 1)
         LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
@@ -774,5 +817,11 @@ int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_b
                             cudaStream_t st) {
     LAUNCH(k_sub_const_chains, (size_t)C * n * ctx->ct_words(), x, out, c_base, C, n, (int)ctx->L, ctx->tab.q,
            ctx->d_delta_q, ctx->t, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_probe_modmul(u64* out, int blocks, int threads, uint32_t iters, u64 q, u64 w, u64 ws, cudaStream_t st) {
+    k_probe_modmul<<<blocks, threads, 0, st>>>(out, iters, q, w, ws);
+    BFHE_LAUNCH_CHECK("k_probe_modmul");
     return BFHE_OK;
 }

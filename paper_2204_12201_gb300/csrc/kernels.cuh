@@ -55,3 +55,4 @@ int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s
                       int select, cudaStream_t st);
 int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, int C, size_t n,
                             cudaStream_t st);
+int launch_probe_modmul(u64* out, int blocks, int threads, uint32_t iters, u64 q, u64 w, u64 ws, cudaStream_t st);

@@ -324,6 +324,7 @@ int ntt_config(int logN, int* log_m, int* log_e) {
 
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
+    ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
     ntt_config((int)ctx->logN, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, 0);
@@ -351,6 +352,7 @@ int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
                    cudaStream_t st) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
+    ProfScope ps(ctx, BFHE_K_NTT_INV, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
     ntt_config((int)ctx->logN, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, mont);
