@@ -170,6 +170,32 @@ enum { BFHE_PAPER = 0, BFHE_SELECT = 1 };
 int bfhe_mod_to_bits(bfhe_ctx* ctx, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
                      uint64_t* bits_out, size_t n, void* stream);
 
+/* Allocation-free variant of bfhe_mul_relin.  The paper has no counterpart:
+ * this is for callers that cannot allocate device memory at call time --
+ * code running under CUDA stream capture (where cudaMalloc and the device
+ * synchronisation that growing the context scratch needs are not allowed),
+ * and deployments that reserve all device memory at start-up and forbid
+ * allocation afterwards.  Same arguments and result as bfhe_mul_relin (bit
+ * identical), but the multiply's scratch is a fixed static device array of
+ * BFHE_NOALLOC_SCRATCH_BYTES (32 MiB) instead of the context's arena; the
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ *  - Size limit: n ciphertexts need n x (4(L+K) + 3L + L(L+alpha) +
+ *    2(L+alpha)) N x 8 bytes of scratch; larger n is rejected with
+ *    BFHE_EINVAL and a message giving the maximum (at N = 16384, L = 8 one
+ *    ciphertext per call; at N = 4096, L = 2, 26).
+ *  - The context's device must be the current device.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress) and
+ *    caches it; make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; no part of it needs to start at zero (every word is written
+ *    before it is read).  Calls that overlap on the GPU (other streams, other
+ *    threads) race on it: serialise them.
+ *  - Every GPU that loads this library keeps the array until the process
+ *    exits. */
+#define BFHE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int bfhe_mul_relin_noalloc(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n,
+                           void* stream);
+
 /* Power by the recursion of Listing 7 (floor(log2 e) + w(e) - 1 multiplies):
  * out[i] = x[i]^e, e >= 1.  out must not alias x. */
 int bfhe_pow(bfhe_ctx* ctx, const uint64_t* x, uint64_t e, uint64_t* out, size_t n, void* stream);

@@ -54,6 +54,7 @@ def load():
         "bfhe_mul_scalar": (I, [P, P, U64, P, S, P]),
         "bfhe_mul_plain": (I, [P, P, P, P, S, P]),
         "bfhe_mul_relin": (I, [P, P, P, P, S, P]),
+        "bfhe_mul_relin_noalloc": (I, [P, P, P, P, S, P]),
         "bfhe_bit_gate": (I, [P, I, P, P, P, P, S, P]),
         "bfhe_gate_level": (I, [P, P, S, S, P, S, S, P]),
         "bfhe_bits_to_mod": (I, [P, P, U32, P, S, P]),
@@ -175,6 +176,10 @@ class Context:
 
     def mul_relin(self, a, b, out=None):
         return self._binary(self.lib.bfhe_mul_relin, a, b, out)
+
+    def mul_relin_noalloc(self, a, b, out=None):
+        """bfhe_mul_relin_noalloc: same product, scratch in the library's static device array."""
+        return self._binary(self.lib.bfhe_mul_relin_noalloc, a, b, out)
 
     def mul_plain(self, a, plain, out=None):
         return self._binary(self.lib.bfhe_mul_plain, a, plain.contiguous(), out)

@@ -1,5 +1,7 @@
 // api.cu -- the C ABI (include/bfhe.h): validation, scratch layout and kernel sequencing.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "kernels.cuh"
 
@@ -567,4 +569,58 @@ extern "C" int bfhe_probe_modmul(int device, uint32_t iters, double* modmul_per_
     cudaFree(buf);
     if (rc == BFHE_OK) *modmul_per_s = (double)blocks * threads * 8.0 * iters / (ms * 1e-3);
     return rc;
+}
+
+// ------------------------------------------------------------------ allocation-free multiply
+// Scratch for bfhe_mul_relin_noalloc: a fixed file-scope device array, so the
+// call itself never allocates.  Every GPU that loads this module holds it until
+// the process exits.  Host code must not pass `g_noalloc_scratch` itself to a
+// kernel (in host code the name is only a stand-in for the symbol); the device
+// address comes from cudaGetSymbolAddress, taken once per device.
+#define BFHE_NOALLOC_WORDS ((size_t)BFHE_NOALLOC_SCRATCH_BYTES / sizeof(u64))
+static __device__ __align__(256) u64 g_noalloc_scratch[BFHE_NOALLOC_WORDS];
+
+namespace {
+std::mutex g_noalloc_mu;
+u64* g_noalloc_ptr[BFHE_MAX_DEVICES] = {};
+
+// device address of the static scratch on the current device (set-up on first use)
+int noalloc_scratch(int device, u64** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_check(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[device] = (u64*)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return BFHE_OK;
+}
+}  // namespace
+
+extern "C" int bfhe_mul_relin_noalloc(bfhe_ctx* c, const uint64_t* a, const uint64_t* b, uint64_t* out, size_t n,
+                                      void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!a || !b || !out) return set_error(BFHE_EINVAL, "null buffer");
+    if (out == a || out == b) return set_error(BFHE_EINVAL, "out must not alias an input");
+    int dev = -1;
+    BFHE_CUDA(cudaGetDevice(&dev));
+    if (dev != c->device || dev < 0 || dev >= BFHE_MAX_DEVICES)
+        return set_error(BFHE_EINVAL, "the context's device must be the current device");
+    const size_t per = mul_words_per_ct(c);
+    const size_t max_n = BFHE_NOALLOC_WORDS / per;
+    if (n > max_n) {
+        return set_error(BFHE_EINVAL, "bfhe_mul_relin_noalloc: " + std::to_string(n) + " ciphertexts need " +
+                                          std::to_string(n * per * sizeof(u64) >> 20) + " MiB of scratch; the static "
+                                          "scratch holds " + std::to_string(BFHE_NOALLOC_SCRATCH_BYTES >> 20) +
+                                          " MiB, i.e. at most " + std::to_string(max_n) +
+                                          " ciphertexts per call at these parameters");
+    }
+    u64* scratch = nullptr;
+    RC(noalloc_scratch(dev, &scratch));
+    RC(mul_relin_impl(c, a, b, out, n, scratch, BFHE_NOALLOC_WORDS, S(stream)));
+    c->counts[2] += n;
+    return BFHE_OK;
 }

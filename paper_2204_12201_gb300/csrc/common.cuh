@@ -22,6 +22,7 @@ typedef unsigned __int128 u128;
 #define BFHE_MAX_L 16
 #define BFHE_MAX_ALPHA 2
 #define BFHE_MAX_PRIMES 64
+#define BFHE_MAX_DEVICES 64
 
 // ------------------------------------------------------------------ device modular arithmetic
 __host__ __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) {
