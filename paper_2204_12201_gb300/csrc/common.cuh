@@ -97,10 +97,8 @@ struct PrimeTab {
     const u64* q;        // modulus
     const u64* qinv;     // -q^-1 mod 2^64
     const u64* mu;       // floor(2^64 / q)
-    const u64* tw;       // [nP][N] psi^brv(k)   forward twiddles
-    const u64* tw_s;
-    const u64* itw;      // [nP][N] psi^-brv(k)  inverse twiddles
-    const u64* itw_s;
+    const u64* tw;       // [nP][N][2] (psi^brv(k), Shoup companion)      forward twiddles
+    const u64* itw;      // [nP][N][2] (psi^-brv(k), Shoup companion)     inverse twiddles
     const u64* fin;      // [nP][8]: inverse last-stage constants (w, ws) x {ninv, ninv*itw[1]} x {plain, Montgomery}
 };
 

@@ -410,7 +410,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     // per-prime tables
     Arena ar;
     std::vector<u64> qv(c->primes), qinv(nP), mu(nP), R2(nP), fin(nP * 8);
-    std::vector<u64> tw((size_t)nP * N), tws((size_t)nP * N), itw((size_t)nP * N), itws((size_t)nP * N);
+    std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2);
     for (uint32_t p = 0; p < nP; ++p) {
         const u64 q = c->primes[p];
         u64 x = q;   // Newton: q * x = 1 mod 2^64
@@ -429,20 +429,20 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
             ipw[k] = mulmod(ipw[k - 1], ipsi, q);
         }
         for (uint32_t k = 0; k < N; ++k) {
-            const size_t o = (size_t)p * N + k;
+            const size_t o = ((size_t)p * N + k) * 2;
             tw[o] = pw[c->brv[k]];
-            tws[o] = shoup_of(tw[o], q);
+            tw[o + 1] = shoup_of(tw[o], q);
             itw[o] = ipw[c->brv[k]];
-            itws[o] = shoup_of(itw[o], q);
+            itw[o + 1] = shoup_of(itw[o], q);
         }
         const u64 ninv = invmod(N % q, q);
-        const u64 w1 = mulmod(ninv, itw[(size_t)p * N + 1], q);
+        const u64 w1 = mulmod(ninv, itw[((size_t)p * N + 1) * 2], q);
         const u64 ninvR = mulmod(ninv, R, q), w1R = mulmod(w1, R, q);
         const u64 f[8] = {ninv, shoup_of(ninv, q), w1, shoup_of(w1, q), ninvR, shoup_of(ninvR, q), w1R, shoup_of(w1R, q)};
         for (int i = 0; i < 8; ++i) fin[p * 8 + i] = f[i];
     }
     const size_t o_q = ar.add(qv), o_qinv = ar.add(qinv), o_mu = ar.add(mu), o_R2 = ar.add(R2), o_fin = ar.add(fin);
-    const size_t o_tw = ar.add(tw), o_tws = ar.add(tws), o_itw = ar.add(itw), o_itws = ar.add(itws);
+    const size_t o_tw = ar.add(tw), o_itw = ar.add(itw);
     std::vector<u64> brv_packed((N + 1) / 2);
     for (uint32_t k = 0; k < N; k += 2)
         brv_packed[k / 2] = (u64)c->brv[k] | ((u64)(k + 1 < N ? c->brv[k + 1] : 0) << 32);
@@ -497,9 +497,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->tab.qinv = base + o_qinv;
     c->tab.mu = base + o_mu;
     c->tab.tw = base + o_tw;
-    c->tab.tw_s = base + o_tws;
     c->tab.itw = base + o_itw;
-    c->tab.itw_s = base + o_itws;
     c->tab.fin = base + o_fin;
     c->d_R2 = base + o_R2;
     c->d_brv = (uint32_t*)(base + o_brv);

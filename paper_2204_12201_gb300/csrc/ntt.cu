@@ -2,10 +2,15 @@
 //
 // Forward: Cooley-Tukey with merged psi twiddles (natural order in, bit-
 // reversed evaluation order out); butterfly on bit b of the index with
-// twiddle psi^brv((N + j) >> (b + 1)); Harvey's lazy butterflies keep values
-// in [0, 4q) and one Shoup product per butterfly.  Inverse: Gentleman-Sande
-// with psi^-brv twiddles, values in [0, 2q), the N^-1 scale (times R = 2^64
-// when the inputs carry a Montgomery factor) merged into the last stage.
+// twiddle psi^brv((N + j) >> (b + 1)) and one Shoup product.  The forward
+// butterfly (X, Y) -> (X + T, X - T + 2q), T = Shoup(Y) in [0, 2q), grows the
+// bound by 2q per stage and is never reduced in between: from inputs < 4q,
+// 15 stages stay below 34q < 2^56 for q < 2^50, and one Barrett-style
+// reduction at the end makes the output canonical.  Inverse: Gentleman-Sande
+// with psi^-brv twiddles, values in [0, 2q) (X + Y reduced by an unsigned
+// min), the N^-1 scale (times R = 2^64 when the inputs carry a Montgomery
+// factor) merged into the last stage.  Twiddles are stored as (w, Shoup(w))
+// pairs and fetched as one 16-byte load.
 //
 // One CTA transforms a block of M = 2^LOG_M <= 16384 consecutive words of a
 // limb held in shared memory; each thread keeps E = 2^LOG_E words in
@@ -16,6 +21,8 @@
 // last pass writes it directly (forward: E consecutive words per thread as
 // 16-byte stores; inverse: coalesced).  For N = 2M the outermost stage runs
 // as a separate elementwise pass.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace {
@@ -53,8 +60,7 @@ __device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx, size_t s
 
 // ---------------------------------------------------------------- forward stages
 template <int LOG_E, int W_LO, int HI, int LO>
-__device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u64* __restrict__ tw,
-                                           const u64* __restrict__ tws, u64 q) {
+__device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw, u64 q) {
     constexpr int E = 1 << LOG_E;
     const u64 q2 = q << 1;
 #pragma unroll
@@ -64,25 +70,23 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
         const u64 base = jb >> (b + 1);
 #pragma unroll
         for (int g = 0; g < (E >> (h + 1)); ++g) {
-            const u64 w = __ldg(tw + base + g);
-            const u64 ws = __ldg(tws + base + g);
+            const ulonglong2 wp = __ldg(tw + base + g);
 #pragma unroll
             for (int r = 0; r < (1 << h); ++r) {
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
-                u64 X = x[e];
-                X = X >= q2 ? X - q2 : X;
-                const u64 T = shoup_lazy(x[e2], w, ws, q);
+                const u64 X = x[e];
+                const u64 T = shoup_lazy(x[e2], wp.x, wp.y, q);
                 x[e] = X + T;
-                x[e2] = X - T + q2;
+                x[e2] = X + q2 - T;
             }
         }
     }
 }
 
 template <int LOG_M, int LOG_E, int P>
-__device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const u64* tw,
-                                         const u64* tws, u64 q, const u64* in, u64* out) {
+__device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* tw,
+                                         u64 q, u64 mu, const u64* in, u64* out) {
     constexpr int E = 1 << LOG_E;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
     constexpr int HI = LOG_M - 1 - P * LOG_E;
@@ -96,21 +100,16 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
     }
-    fwd_stages<LOG_E, W_LO, HI, LO>(x, jglob + base, tw, tws, q);
+    fwd_stages<LOG_E, W_LO, HI, LO>(x, jglob + base, tw, q);
     if constexpr (P + 1 < NPASS) {
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         __syncthreads();
-        fwd_pass<LOG_M, LOG_E, P + 1>(x, sm, tid, jglob, tw, tws, q, in, out);
+        fwd_pass<LOG_M, LOG_E, P + 1>(x, sm, tid, jglob, tw, q, mu, in, out);
     } else {
-        // W_LO == 0 here: E consecutive words per thread
-        const u64 q2 = q << 1;
+        // W_LO == 0 here: E consecutive words per thread; values < 34q -> canonical
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            u64 v = x[e];
-            v = v >= q2 ? v - q2 : v;
-            x[e] = v >= q ? v - q : v;
-        }
+        for (int e = 0; e < E; ++e) x[e] = reduce64(x[e], q, mu);
         ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + base);
 #pragma unroll
         for (int e = 0; e < E / 2; ++e) o2[e] = make_ulonglong2(x[2 * e], x[2 * e + 1]);
@@ -121,12 +120,11 @@ template <int LOG_M, int LOG_E>
 __global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_fwd(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
-    const u64 q = a.tab.q[lp.p];
-    const u64* tw = a.tab.tw + (size_t)lp.p * a.N;
-    const u64* tws = a.tab.tw_s + (size_t)lp.p * a.N;
+    const u64 q = a.tab.q[lp.p], mu = a.tab.mu[lp.p];
+    const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(a.tab.tw) + (size_t)lp.p * a.N;
     const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
     u64 x[1 << LOG_E];
-    fwd_pass<LOG_M, LOG_E, 0>(x, sm, threadIdx.x, jglob, tw, tws, q, lp.in, lp.out);
+    fwd_pass<LOG_M, LOG_E, 0>(x, sm, threadIdx.x, jglob, tw, q, mu, lp.in, lp.out);
 }
 
 // outermost stage (bit logN - 1) for N = 2M, elementwise; inputs < 4q, outputs lazily < 4q
@@ -134,7 +132,7 @@ __global__ void k_ntt_fwd_top(NttArgs a) {
     const int half = a.N >> 1;
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x, 0);
     const u64 q = a.tab.q[lp.p], q2 = q << 1;
-    const u64 w = a.tab.tw[(size_t)lp.p * a.N + 1], ws = a.tab.tw_s[(size_t)lp.p * a.N + 1];
+    const u64 w = a.tab.tw[((size_t)lp.p * a.N + 1) * 2], ws = a.tab.tw[((size_t)lp.p * a.N + 1) * 2 + 1];
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
         u64 X = lp.in[j];
         X = X >= q2 ? X - q2 : X;
@@ -145,9 +143,11 @@ __global__ void k_ntt_fwd_top(NttArgs a) {
 }
 
 // ---------------------------------------------------------------- inverse stages
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+
 template <int LOG_E, int W_LO, int LO, int HI, bool SCALE_TOP>
-__device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const u64* __restrict__ itw,
-                                           const u64* __restrict__ itws, u64 q, const u64* fin) {
+__device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ itw, u64 q,
+                                           const u64* fin) {
     constexpr int E = 1 << LOG_E;
     const u64 q2 = q << 1;
 #pragma unroll
@@ -165,23 +165,21 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
                     const int e2 = e | (1 << h);
                     const u64 X = x[e], Y = x[e2];
                     x[e] = shoup(X + Y, n0, n0s, q);
-                    x[e2] = shoup(X - Y + q2, n1, n1s, q);
+                    x[e2] = shoup(X + q2 - Y, n1, n1s, q);
                 }
             }
         } else {
 #pragma unroll
             for (int g = 0; g < (E >> (h + 1)); ++g) {
-                const u64 w = __ldg(itw + base + g);
-                const u64 ws = __ldg(itws + base + g);
+                const ulonglong2 wp = __ldg(itw + base + g);
 #pragma unroll
                 for (int r = 0; r < (1 << h); ++r) {
                     const int e = (g << (h + 1)) | r;
                     const int e2 = e | (1 << h);
                     const u64 X = x[e], Y = x[e2];
-                    u64 S = X + Y;
-                    S = S >= q2 ? S - q2 : S;
-                    x[e] = S;
-                    x[e2] = shoup_lazy(X - Y + q2, w, ws, q);
+                    const u64 S = X + Y;
+                    x[e] = umin64(S, S - q2);
+                    x[e2] = shoup_lazy(X + q2 - Y, wp.x, wp.y, q);
                 }
             }
         }
@@ -189,8 +187,8 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
 }
 
 template <int LOG_M, int LOG_E, int P, bool FULL>
-__device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const u64* itw,
-                                         const u64* itws, u64 q, const u64* fin, const u64* in, u64* out) {
+__device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* itw,
+                                         u64 q, const u64* fin, const u64* in, u64* out) {
     constexpr int E = 1 << LOG_E;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
     constexpr int LO = P * LOG_E;
@@ -211,12 +209,12 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
     }
     constexpr bool LAST = (P + 1 == NPASS);
-    inv_stages<LOG_E, W_LO, LO, HI, FULL && LAST>(x, jglob + base, itw, itws, q, fin);
+    inv_stages<LOG_E, W_LO, LO, HI, FULL && LAST>(x, jglob + base, itw, q, fin);
     if constexpr (!LAST) {
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         __syncthreads();
-        inv_pass<LOG_M, LOG_E, P + 1, FULL>(x, sm, tid, jglob, itw, itws, q, fin, in, out);
+        inv_pass<LOG_M, LOG_E, P + 1, FULL>(x, sm, tid, jglob, itw, q, fin, in, out);
     } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) out[base + (e << W_LO)] = x[e];
@@ -228,12 +226,11 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_inv(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
     const u64 q = a.tab.q[lp.p];
-    const u64* itw = a.tab.itw + (size_t)lp.p * a.N;
-    const u64* itws = a.tab.itw_s + (size_t)lp.p * a.N;
+    const ulonglong2* itw = reinterpret_cast<const ulonglong2*>(a.tab.itw) + (size_t)lp.p * a.N;
     const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
     const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
     u64 x[1 << LOG_E];
-    inv_pass<LOG_M, LOG_E, 0, FULL>(x, sm, threadIdx.x, jglob, itw, itws, q, fin, lp.in, lp.out);
+    inv_pass<LOG_M, LOG_E, 0, FULL>(x, sm, threadIdx.x, jglob, itw, q, fin, lp.in, lp.out);
 }
 
 // outermost inverse stage with the N^-1 scale, for N = 2M; inputs < 2q, outputs canonical
@@ -246,7 +243,7 @@ __global__ void k_ntt_inv_top(NttArgs a) {
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
         const u64 X = lp.out[j], Y = lp.out[j + half];
         lp.out[j] = shoup(X + Y, n0, n0s, q);
-        lp.out[j + half] = shoup(X - Y + q2, n1, n1s, q);
+        lp.out[j + half] = shoup(X + q2 - Y, n1, n1s, q);
     }
 }
 
@@ -309,9 +306,15 @@ NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map
 void ntt_set_log_e(int log_e) { g_log_e_override = log_e; }
 
 int ntt_config(int logN, int* log_m, int* log_e) {
+    static int env_e = [] {
+        const char* s = getenv("BFHE_NTT_LOG_E");
+        return s ? atoi(s) : 0;
+    }();
     *log_m = logN > 14 ? 14 : logN;
-    int e = 4;
+    int e = *log_m == 14 ? 5 : 4;   // 512 x 128-register threads for 16384-word blocks
+    if (env_e >= 3 && env_e <= 5) e = env_e;
     if (g_log_e_override >= 3 && g_log_e_override <= 5) e = g_log_e_override;
+    if (*log_m == 14 && e < 4) e = 4;
     *log_e = e;
     return BFHE_OK;
 }
