@@ -55,9 +55,19 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         const u64* a = A + c0 * ctw;
         const u64* b = B + c0 * ctw;
         u64* o = out + c0 * ctw;
-        RC(launch_modup(c, a, b, X, m, st));
-        RC(launch_ntt_fwd(c, ntt_io(X, X, LK, N), 4 * m, (int)LK, c->mapQB(), st));
-        RC(launch_tensor(c, X, m, st));
+        // a squaring (a == b) extends and transforms a0, a1 only; the tensor sums are the same
+        const int sq = (A == B) ? 1 : 0;
+        const int slots = sq ? 2 : 4;
+        RC(launch_modup(c, a, b, X, m, slots, st));
+        NttIO iox;
+        iox.in = X;
+        iox.out = X;
+        iox.n_inner = slots;
+        iox.in_os = iox.out_os = 4 * LK * N;
+        iox.in_is = iox.out_is = LK * N;
+        iox.in_ls = iox.out_ls = N;
+        RC(launch_ntt_fwd(c, iox, slots * m, (int)LK, c->mapQB(), st));
+        RC(launch_tensor(c, X, m, sq, st));
         NttIO io3;
         io3.in = X;
         io3.out = X;

@@ -147,6 +147,30 @@ __global__ void k_tensor(u64* X, int n, int LK, LimbMap map, PrimeTab tab, int N
     }
 }
 
+// squaring: X[c][0..1] = (a0, a1) -> X[c][0..2] = (a0^2, 2 a0 a1, a1^2), same sums as the general tensor
+__global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, int N) {
+    const size_t plane = (size_t)LK * N;
+    const size_t total = (size_t)n * plane;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = idx / plane, off = idx % plane;
+        const int limb = (int)(off / N);
+        const int pi = map(limb);
+        const u64 q = tab.q[pi], qinv = tab.qinv[pi];
+        u64* x = X + c * 4 * plane + off;
+        const u64 a0 = x[0], a1 = x[plane];
+        const u64 d0 = redc(__umul64hi(a0, a0), a0 * a0, q, qinv);
+        u64 hi = 0, lo = 0;
+        mac128(hi, lo, a0, a1);
+        mac128(hi, lo, a1, a0);
+        const u64 d1 = redc(hi, lo, q, qinv);
+        const u64 d2 = redc(__umul64hi(a1, a1), a1 * a1, q, qinv);
+        x[0] = d0;
+        x[plane] = d1;
+        x[2 * plane] = d2;
+    }
+}
+
 // key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC)
 template <int CB>
 __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int L, int QP, PrimeTab tab, int N) {
@@ -187,6 +211,8 @@ __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int L, int
 }
 
 // ---------------------------------------------------------------- exact base extension
+// Inputs x_i may be lazy (< 2 s_i); digits come out canonical.  Inner steps keep
+// u in [0, 2 s_i): u + s_i - v_j < 3 s_i goes straight into a lazy Shoup product.
 template <int NS>
 __device__ __forceinline__ bool garner(const u64 (&x)[NS], const ExtDesc& d, u64 (&v)[NS]) {
 #pragma unroll
@@ -197,9 +223,9 @@ __device__ __forceinline__ bool garner(const u64 (&x)[NS], const ExtDesc& d, u64
         for (int j = 0; j < i; ++j) {
             u64 vj = v[j];
             vj = vj >= si ? vj - si : vj;
-            u = u >= vj ? u - vj : u + si - vj;
-            u = shoup(u, d.ginv[i * NS + j], d.ginv_s[i * NS + j], si);
+            u = shoup_lazy(u + si - vj, d.ginv[i * NS + j], d.ginv_s[i * NS + j], si);
         }
+        u = u >= si ? u - si : u;
         v[i] = u;
     }
     int state = 0;
@@ -211,39 +237,46 @@ __device__ __forceinline__ bool garner(const u64 (&x)[NS], const ExtDesc& d, u64
     return state > 0;   // x > (S-1)/2: the centred value is x - S
 }
 
-// value mod T_j of the centred integer with digits v (SMALL: T may be far below the sources)
+// value mod T_j of the centred integer with digits v (SMALL: T may be far below the sources).
+// Without SMALL every digit is < 2 T_j, so Horner runs lazily below 4 T_j.
 template <int NS, bool SMALL>
 __device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtDesc& d, int j) {
     const u64 T = d.dst_q[j];
-    const u64 mu = d.dst_mu[j];
-    auto red = [&](u64 a) -> u64 {
-        if (SMALL) return reduce64(a, T, mu);
-        a = a >= T ? a - T : a;
-        return a >= T ? a - T : a;
-    };
-    u64 acc = red(v[NS - 1]);
+    u64 acc;
+    if (SMALL) {
+        const u64 mu = d.dst_mu[j];
+        acc = reduce64(v[NS - 1], T, mu);
 #pragma unroll
-    for (int i = NS - 2; i >= 0; --i) {
-        acc = shoup(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T);
-        acc = add_mod(acc, red(v[i]), T);
+        for (int i = NS - 2; i >= 0; --i) {
+            acc = shoup(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T);
+            acc = add_mod(acc, reduce64(v[i], T, mu), T);
+        }
+    } else {
+        acc = v[NS - 1];
+#pragma unroll
+        for (int i = NS - 2; i >= 0; --i)
+            acc = shoup_lazy(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T) + v[i];
+        const u64 T2 = T << 1;
+        acc = acc >= T2 ? acc - T2 : acc;
+        acc = acc >= T ? acc - T : acc;
     }
     if (neg) acc = sub_mod(acc, d.smod[j], T);
     return acc;
 }
 
-// X[pp] (pp = 4c + slot, slots a0 a1 b0 b1): Q limbs copied, B limbs = centred extension
+// X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
 template <int NS>
-__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int K, ExtDesc ext, int N) {
-    const size_t total = (size_t)n * 4 * N;
+__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N) {
+    const size_t total = (size_t)n * slots * N;
     const int LK = NS + K;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(idx % N);
         const size_t pp = idx / N;
-        const size_t c = pp >> 2;
-        const int slot = (int)(pp & 3);
+        const size_t c = pp / slots;
+        const int slot = (int)(pp % slots);
         const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)NS * N + k;
-        u64* dst = X + pp * (size_t)LK * N + k;
+        u64* dst = X + (c * 4 + slot) * (size_t)LK * N + k;
         u64 x[NS], v[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -272,7 +305,7 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const u64 qi = eQB.src_q[i];
-            r[i] = shoup(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);      // [t d]_{q_i}
+            r[i] = shoup_lazy(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);   // [t d]_{q_i}, < 2 q_i
         }
         const bool neg = garner<NS>(r, eQB, v);
         u64 y[KS], w[KS];
@@ -280,9 +313,9 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
         for (int j = 0; j < KS; ++j) {
             const u64 bj = bq[j];
             const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
-            const u64 td = shoup(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);
+            const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);   // < 2 b_j
             const u64 rb = ext_eval<NS, false>(v, neg, eQB, j);
-            y[j] = shoup(sub_mod(td, rb, bj), Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q
+            y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
         }
         const bool negy = garner<KS>(y, eBQ, w);
         u64* o = C3 + cp * (size_t)NS * N + k;
@@ -645,10 +678,13 @@ int launch_pointwise(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* out, 
     return BFHE_OK;
 }
 
-int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, cudaStream_t st) {
+int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, int square, cudaStream_t st) {
     ProfScope ps(ctx, BFHE_K_TENSOR, st, 4.0 * n * (ctx->L + ctx->K) * ctx->N);
     const int LK = (int)(ctx->L + ctx->K);
-    LAUNCH(k_tensor, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
+    if (square)
+        LAUNCH(k_tensor_sq, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
+    else
+        LAUNCH(k_tensor, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
     return BFHE_OK;
 }
 
@@ -662,9 +698,9 @@ int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t
 }
 
 template <int NS>
-int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, cudaStream_t st) {
-    const size_t work = (size_t)n * 4 * ctx->N;
-    LAUNCH(k_modup<NS>, work, A, B, X, n, (int)ctx->K, ctx->ext_QB, (int)ctx->N);
+int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
+    const size_t work = (size_t)n * slots * ctx->N;
+    LAUNCH(k_modup<NS>, work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N);
     return BFHE_OK;
 }
 
@@ -705,10 +741,10 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
         default: return set_error(BFHE_EINVAL, "unsupported number of data primes");                         \
     }
 
-int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, cudaStream_t st) {
+int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const double L_ = ctx->L, K_ = ctx->K;
-    ProfScope ps(ctx, BFHE_K_MODUP, st, 4.0 * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
-    SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, st)
+    ProfScope ps(ctx, BFHE_K_MODUP, st, (double)slots * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
+    SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, slots, st)
 }
 
 int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {

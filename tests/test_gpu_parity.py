@@ -237,3 +237,15 @@ def test_gate_level_matches_gates():
     for i, g in enumerate(gates):
         want = bridge.Evaluator(prm, P.keys).gate(g, *cts)
         assert_ct_equal(prm, wires[3 + i], [want], "level gate %s" % bridge.GATE_NAMES[g])
+
+
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("ALPHA2", ALPHA2)])
+def test_square_path(name, cfg):
+    """mul_relin(x, x) through the squaring path equals the oracle's x * x."""
+    P = pair(name, cfg)
+    prm = P.prm
+    y = inputs.slots(19, 2, prm.N, hi=prm.t)
+    xs = [P.enc(y[i], 111, i) for i in range(2)]
+    d = cts_to_device(prm, xs)
+    got = P.ctx.mul_relin(d, d)
+    assert_ct_equal(prm, got, [bfv.mul_relin(prm, P.keys, x, x) for x in xs], "square")
