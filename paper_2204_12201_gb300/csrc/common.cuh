@@ -45,6 +45,17 @@ __host__ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) 
     return a * w - mulhi64(a, ws) * q;
 }
 
+// a * w mod q in [0, 3q) for a < 2^64: the quotient estimate drops the low 32x32
+// partial product of a * ws, so it is floor(a ws / 2^64) or one less (three wide
+// 32x32 products instead of four).
+__host__ __device__ __forceinline__ u64 shoup_lazy3(u64 a, u64 w, u64 ws, u64 q) {
+    const u64 a1 = a >> 32, a0 = a & 0xffffffffull, w1 = ws >> 32, w0 = ws & 0xffffffffull;
+    const u64 p10 = a1 * w0, p01 = a0 * w1;
+    const u64 mid = p10 + p01;
+    const u64 hi = a1 * w1 + (mid >> 32) + (mid < p10 ? (1ull << 32) : 0ull);
+    return a * w - hi * q;
+}
+
 __host__ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
     u64 r = shoup_lazy(a, w, ws, q);
     return r >= q ? r - q : r;
@@ -222,5 +233,5 @@ int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
 // mont != 0: the final scale is N^-1 R (undoes one Montgomery factor R^-1 of the inputs)
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
                    cudaStream_t st);
-int ntt_config(int logN, int* log_m, int* log_e);
+int ntt_config(int logN, int inverse, int* log_m, int* log_e);
 void ntt_set_log_e(int log_e);   // tuning override (0 = default)

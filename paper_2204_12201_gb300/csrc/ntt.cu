@@ -3,27 +3,40 @@
 // Forward: Cooley-Tukey with merged psi twiddles (natural order in, bit-
 // reversed evaluation order out); butterfly on bit b of the index with
 // twiddle psi^brv((N + j) >> (b + 1)) and one Shoup product.  The forward
-// butterfly (X, Y) -> (X + T, X - T + 2q), T = Shoup(Y) in [0, 2q), grows the
-// bound by 2q per stage and is never reduced in between: from inputs < 4q,
-// 15 stages stay below 34q < 2^56 for q < 2^50, and one Barrett-style
-// reduction at the end makes the output canonical.  Inverse: Gentleman-Sande
-// with psi^-brv twiddles, values in [0, 2q) (X + Y reduced by an unsigned
-// min), the N^-1 scale (times R = 2^64 when the inputs carry a Montgomery
-// factor) merged into the last stage.  Twiddles are stored as (w, Shoup(w))
-// pairs and fetched as one 16-byte load.
+// butterfly (X, Y) -> (X + T, X - T + 3q), T = Shoup(Y) in [0, 3q) (the
+// quotient estimate may be one short, see shoup_lazy3), grows the bound by 3q
+// per stage and is never reduced in between: from inputs < 4q, 15 stages stay
+// below 49q < 2^56 for q < 2^50, and one Barrett-style reduction at the end
+// makes the output canonical.  Inverse: Gentleman-Sande with psi^-brv
+// twiddles and exact Shoup products, values in [0, 2q) (X + Y reduced by an
+// unsigned min), the N^-1 scale (times R = 2^64 when the inputs carry a
+// Montgomery factor) merged into the last stage.  Twiddles are stored as
+// (w, Shoup(w)) pairs and fetched as one 16-byte load.
 //
-// One CTA transforms a block of M = 2^LOG_M <= 16384 consecutive words of a
-// limb held in shared memory; each thread keeps E = 2^LOG_E words in
-// registers and runs up to LOG_E radix-2 stages on them per pass, with one
-// padded shared-memory exchange (one pad word per 16, conflict-free for
-// every window) and one barrier between passes.  The first pass reads global
-// memory directly (coalesced: lanes differ in the low index bits) and the
-// last pass writes it directly (forward: E consecutive words per thread as
-// 16-byte stores; inverse: coalesced).  For N = 2M the outermost stage runs
-// as a separate elementwise pass.
+// One CTA transforms a block of M = 2^LOG_M words of a limb held in shared
+// memory; each thread keeps E = 2^LOG_E words in registers and runs up to
+// LOG_E radix-2 stages on them per pass, with one padded shared-memory
+// exchange (one pad word per 16, conflict-free for every window) and one
+// barrier between passes.  The first pass reads global memory directly
+// (coalesced: lanes differ in the low index bits) and the last pass writes it
+// directly (forward: E consecutive words per thread as 16-byte stores;
+// inverse: coalesced).
+//
+// When N = 2M a limb is split over two CTAs (so that two of them share an SM
+// at N = 16384).  Forward: the outermost stage pairs word j of the first half
+// with word j of the second; each CTA reads both halves in its first pass and
+// keeps the output of its own half, so the stage costs no extra pass.
+// Inverse: the two CTAs form a thread-block cluster; after the inner stages
+// each publishes its half in shared memory, reads the partner's through
+// distributed shared memory and finishes the outermost stage (with the N^-1
+// scale) for its own half.
+#include <cooperative_groups.h>
+
 #include <cstdlib>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -42,18 +55,18 @@ struct NttArgs {
 };
 
 struct LimbPtrs {
-    const u64* in;
-    u64* out;
+    const u64* in;   // limb start
+    u64* out;        // limb start
     int p;
 };
 
-__device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx, size_t sub_off) {
+__device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx) {
     const int limb = bx % a.n_limbs;
     const int poly = bx / a.n_limbs;
     const int outer = poly / a.n_inner, inner = poly % a.n_inner;
     LimbPtrs r;
-    r.in = a.in + outer * a.in_os + inner * a.in_is + limb * a.in_ls + sub_off;
-    r.out = a.out + outer * a.out_os + inner * a.out_is + limb * a.out_ls + sub_off;
+    r.in = a.in + outer * a.in_os + inner * a.in_is + limb * a.in_ls;
+    r.out = a.out + outer * a.out_os + inner * a.out_is + limb * a.out_ls;
     r.p = a.map(limb);
     return r;
 }
@@ -62,7 +75,7 @@ __device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx, size_t s
 template <int LOG_E, int W_LO, int HI, int LO>
 __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q2 = q << 1;
+    const u64 q3 = 3 * q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = HI - st;
@@ -76,26 +89,40 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
                 const u64 X = x[e];
-                const u64 T = shoup_lazy(x[e2], wp.x, wp.y, q);
+                const u64 T = shoup_lazy3(x[e2], wp.x, wp.y, q);
                 x[e] = X + T;
-                x[e2] = X + q2 - T;
+                x[e2] = X + q3 - T;
             }
         }
     }
 }
 
-template <int LOG_M, int LOG_E, int P>
+// TOP: this CTA is half `half` of a limb of N = 2M words and first applies the
+// outermost stage (twiddle psi^brv(1)) to the pairs (j, j + M) it reads.
+template <int LOG_M, int LOG_E, int P, bool TOP>
 __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* tw,
-                                         u64 q, u64 mu, const u64* in, u64* out) {
+                                         u64 q, u64 mu, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
+    constexpr int M = 1 << LOG_M;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
     constexpr int HI = LOG_M - 1 - P * LOG_E;
     constexpr int LO = (HI - LOG_E + 1) > 0 ? (HI - LOG_E + 1) : 0;
     constexpr int W_LO = LO;
     const int base = (tid & ((1 << W_LO) - 1)) | ((tid >> W_LO) << (W_LO + LOG_E));
     if (P == 0) {
+        if (TOP) {
+            const ulonglong2 w1 = __ldg(tw + 1);
+            const u64 q3 = 3 * q;
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = in[base + (e << W_LO)];
+            for (int e = 0; e < E; ++e) {
+                const u64 X = in[base + (e << W_LO)];
+                const u64 T = shoup_lazy3(in[M + base + (e << W_LO)], w1.x, w1.y, q);
+                x[e] = half ? X + q3 - T : X + T;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = in[base + (e << W_LO)];
+        }
     } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
@@ -105,9 +132,9 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         __syncthreads();
-        fwd_pass<LOG_M, LOG_E, P + 1>(x, sm, tid, jglob, tw, q, mu, in, out);
+        fwd_pass<LOG_M, LOG_E, P + 1, TOP>(x, sm, tid, jglob, tw, q, mu, in, out, half);
     } else {
-        // W_LO == 0 here: E consecutive words per thread; values < 34q -> canonical
+        // W_LO == 0 here: E consecutive words per thread; values < 49q -> canonical
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = reduce64(x[e], q, mu);
         ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + base);
@@ -116,30 +143,17 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
     }
 }
 
-template <int LOG_M, int LOG_E>
-__global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_fwd(NttArgs a) {
+template <int LOG_M, int LOG_E, bool TOP>
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 ? 2 : 1)) k_ntt_fwd(NttArgs a) {
     extern __shared__ u64 sm[];
-    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
+    const int half = blockIdx.y;
     const u64 q = a.tab.q[lp.p], mu = a.tab.mu[lp.p];
     const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(a.tab.tw) + (size_t)lp.p * a.N;
-    const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
+    const u64 jglob = (u64)a.N + ((u64)half << LOG_M);
+    const u64* in = TOP ? lp.in : lp.in + ((size_t)half << LOG_M);
     u64 x[1 << LOG_E];
-    fwd_pass<LOG_M, LOG_E, 0>(x, sm, threadIdx.x, jglob, tw, q, mu, lp.in, lp.out);
-}
-
-// outermost stage (bit logN - 1) for N = 2M, elementwise; inputs < 4q, outputs lazily < 4q
-__global__ void k_ntt_fwd_top(NttArgs a) {
-    const int half = a.N >> 1;
-    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, 0);
-    const u64 q = a.tab.q[lp.p], q2 = q << 1;
-    const u64 w = a.tab.tw[((size_t)lp.p * a.N + 1) * 2], ws = a.tab.tw[((size_t)lp.p * a.N + 1) * 2 + 1];
-    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
-        u64 X = lp.in[j];
-        X = X >= q2 ? X - q2 : X;
-        const u64 T = shoup_lazy(lp.in[j + half], w, ws, q);
-        lp.out[j] = X + T;
-        lp.out[j + half] = X - T + q2;
-    }
+    fwd_pass<LOG_M, LOG_E, 0, TOP>(x, sm, threadIdx.x, jglob, tw, q, mu, in, lp.out + ((size_t)half << LOG_M), half);
 }
 
 // ---------------------------------------------------------------- inverse stages
@@ -186,9 +200,11 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
     }
 }
 
-template <int LOG_M, int LOG_E, int P, bool FULL>
+// MODE 1: the block is the whole limb (scale in the last stage); MODE 2: half `half`
+// of a limb of N = 2M words, finished through the partner CTA of the cluster.
+template <int LOG_M, int LOG_E, int P, int MODE>
 __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* itw,
-                                         u64 q, const u64* fin, const u64* in, u64* out) {
+                                         u64 q, const u64* fin, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
     constexpr int LO = P * LOG_E;
@@ -209,75 +225,100 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
     }
     constexpr bool LAST = (P + 1 == NPASS);
-    inv_stages<LOG_E, W_LO, LO, HI, FULL && LAST>(x, jglob + base, itw, q, fin);
+    inv_stages<LOG_E, W_LO, LO, HI, MODE == 1 && LAST>(x, jglob + base, itw, q, fin);
     if constexpr (!LAST) {
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         __syncthreads();
-        inv_pass<LOG_M, LOG_E, P + 1, FULL>(x, sm, tid, jglob, itw, q, fin, in, out);
+        inv_pass<LOG_M, LOG_E, P + 1, MODE>(x, sm, tid, jglob, itw, q, fin, in, out, half);
+    } else if constexpr (MODE == 2) {
+        // outermost stage across the two halves: publish, then read the partner's words
+        // at the same block positions through distributed shared memory
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        cl.sync();
+        const u64* peer = cl.map_shared_rank(sm, cl.block_rank() ^ 1u);
+        const u64 q2 = q << 1;
+        const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const u64 mine = x[e], other = peer[phys(base + (e << W_LO))];
+            out[base + (e << W_LO)] = half ? shoup(other + q2 - mine, n1, n1s, q) : shoup(mine + other, n0, n0s, q);
+        }
+        cl.sync();   // the partner has finished reading this CTA's shared memory
     } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) out[base + (e << W_LO)] = x[e];
     }
 }
 
-template <int LOG_M, int LOG_E, bool FULL>
-__global__ void __launch_bounds__(1 << (LOG_M - LOG_E)) k_ntt_inv(NttArgs a) {
+template <int LOG_M, int LOG_E, int MODE>
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14 ? 2 : 1)) k_ntt_inv(NttArgs a) {
     extern __shared__ u64 sm[];
-    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, (size_t)blockIdx.y << LOG_M);
+    const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
+    const int half = blockIdx.y;
     const u64 q = a.tab.q[lp.p];
     const ulonglong2* itw = reinterpret_cast<const ulonglong2*>(a.tab.itw) + (size_t)lp.p * a.N;
     const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
-    const u64 jglob = (u64)a.N + ((u64)blockIdx.y << LOG_M);
+    const u64 jglob = (u64)a.N + ((u64)half << LOG_M);
     u64 x[1 << LOG_E];
-    inv_pass<LOG_M, LOG_E, 0, FULL>(x, sm, threadIdx.x, jglob, itw, q, fin, lp.in, lp.out);
-}
-
-// outermost inverse stage with the N^-1 scale, for N = 2M; inputs < 2q, outputs canonical
-__global__ void k_ntt_inv_top(NttArgs a) {
-    const int half = a.N >> 1;
-    const LimbPtrs lp = limb_ptrs(a, blockIdx.x, 0);
-    const u64 q = a.tab.q[lp.p], q2 = q << 1;
-    const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
-    const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
-    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < half; j += gridDim.y * blockDim.x) {
-        const u64 X = lp.out[j], Y = lp.out[j + half];
-        lp.out[j] = shoup(X + Y, n0, n0s, q);
-        lp.out[j + half] = shoup(X + q2 - Y, n1, n1s, q);
-    }
+    inv_pass<LOG_M, LOG_E, 0, MODE>(x, sm, threadIdx.x, jglob, itw, q, fin, lp.in + ((size_t)half << LOG_M),
+                                    lp.out + ((size_t)half << LOG_M), half);
 }
 
 int g_log_e_override = 0;
 
 template <int LOG_M, int LOG_E>
-int run_fwd(const NttArgs& a, int blocks, int subs, cudaStream_t st) {
+constexpr size_t smem_bytes() {
+    return (LOG_M + LOG_E - 1) / LOG_E > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
+}
+
+template <int LOG_M, int LOG_E, bool TOP>
+int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
-    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
-    const size_t smem = NPASS > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
+    const size_t smem = smem_bytes<LOG_M, LOG_E>();
     static bool attr = false;
     if (!attr) {
-        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E, TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         attr = true;
     }
-    k_ntt_fwd<LOG_M, LOG_E><<<dim3(blocks, subs), T, smem, st>>>(a);
+    k_ntt_fwd<LOG_M, LOG_E, TOP><<<dim3(blocks, TOP ? 2 : 1), T, smem, st>>>(a);
     BFHE_LAUNCH_CHECK("k_ntt_fwd");
     return BFHE_OK;
 }
 
-template <int LOG_M, int LOG_E, bool FULL>
-int run_inv(const NttArgs& a, int blocks, int subs, cudaStream_t st) {
+template <int LOG_M, int LOG_E, int MODE>
+int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
-    constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
-    const size_t smem = NPASS > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
+    // the cluster exchange needs the shared buffer even for a single pass
+    const size_t smem = MODE == 2 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : smem_bytes<LOG_M, LOG_E>();
     static bool attr = false;
     if (!attr) {
-        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         attr = true;
     }
-    k_ntt_inv<LOG_M, LOG_E, FULL><<<dim3(blocks, subs), T, smem, st>>>(a);
-    BFHE_LAUNCH_CHECK("k_ntt_inv");
+    if (MODE == 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks, 2, 1);
+        cfg.blockDim = dim3(T, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = 2;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_inv<LOG_M, LOG_E, MODE>, a));
+        BFHE_LAUNCH_CHECK("k_ntt_inv (cluster)");
+    } else {
+        k_ntt_inv<LOG_M, LOG_E, MODE><<<dim3(blocks, 1), T, smem, st>>>(a);
+        BFHE_LAUNCH_CHECK("k_ntt_inv");
+    }
     return BFHE_OK;
 }
 
@@ -301,49 +342,51 @@ NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map
     return a;
 }
 
+int env_int(const char* name) {
+    const char* s = getenv(name);
+    return s ? atoi(s) : 0;
+}
+
 }  // namespace
 
 void ntt_set_log_e(int log_e) { g_log_e_override = log_e; }
 
-int ntt_config(int logN, int* log_m, int* log_e) {
-    static int env_e = [] {
-        const char* s = getenv("BFHE_NTT_LOG_E");
-        return s ? atoi(s) : 0;
-    }();
-    *log_m = logN > 14 ? 14 : logN;
-    int e = *log_m == 14 ? 5 : 4;   // 512 x 128-register threads for 16384-word blocks
+// Block size and registers per thread (measured on GB300): N <= 8192 in one
+// block; N = 16384 forward as two 8192-word halves (two CTAs per SM), inverse
+// in one block; N = 32768 as two 16384-word halves.  BFHE_NTT_LOG_M /
+// BFHE_NTT_LOG_E override (tuning).
+int ntt_config(int logN, int inverse, int* log_m, int* log_e) {
+    static const int env_m = env_int("BFHE_NTT_LOG_M");
+    static const int env_e = env_int("BFHE_NTT_LOG_E");
+    int m = logN <= 13 ? logN : logN - 1;
+    if (inverse && logN == 14) m = 14;
+    if (env_m >= logN - 1 && env_m <= logN && env_m >= 10 && env_m <= 14) m = env_m;
+    int e = (m == 14 || (m == 13 && logN == 14)) ? 5 : 4;
     if (env_e >= 3 && env_e <= 5) e = env_e;
     if (g_log_e_override >= 3 && g_log_e_override <= 5) e = g_log_e_override;
-    if (*log_m == 14 && e < 4) e = 4;
+    if (m == 14 && e < 4) e = 4;
+    *log_m = m;
     *log_e = e;
     return BFHE_OK;
 }
 
-#define FWD_CASE(LM, LE) \
-    if (log_m == LM && log_e == LE) return run_fwd<LM, LE>(a, blocks, subs, st);
-#define INV_CASE(LM, LE)                                                        \
-    if (log_m == LM && log_e == LE)                                              \
-        return full ? run_inv<LM, LE, true>(a, blocks, subs, st) : run_inv<LM, LE, false>(a, blocks, subs, st);
+#define FWD_CASE(LM, LE)                                                                                   \
+    if (log_m == LM && log_e == LE)                                                                         \
+        return top ? run_fwd<LM, LE, true>(a, blocks, st) : run_fwd<LM, LE, false>(a, blocks, st);
+#define INV_CASE(LM, LE)                                                                                   \
+    if (log_m == LM && log_e == LE)                                                                         \
+        return split ? run_inv<LM, LE, 2>(a, blocks, st) : run_inv<LM, LE, 1>(a, blocks, st);
 
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
     ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
-    ntt_config((int)ctx->logN, &log_m, &log_e);
+    ntt_config((int)ctx->logN, 0, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, 0);
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
-    if (subs == 2) {
-        k_ntt_fwd_top<<<dim3(blocks, 8), 256, 0, st>>>(a);
-        BFHE_LAUNCH_CHECK("k_ntt_fwd_top");
-        // the block pass continues in place on the output
-        a.in = a.out;
-        a.in_os = a.out_os;
-        a.in_is = a.out_is;
-        a.in_ls = a.out_ls;
-    } else if (subs != 1) {
-        return set_error(BFHE_EINVAL, "unsupported ring degree");
-    }
+    if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
+    const bool top = subs == 2;
     FWD_CASE(10, 3) FWD_CASE(10, 4) FWD_CASE(10, 5)
     FWD_CASE(11, 3) FWD_CASE(11, 4) FWD_CASE(11, 5)
     FWD_CASE(12, 3) FWD_CASE(12, 4) FWD_CASE(12, 5)
@@ -357,22 +400,16 @@ int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
     ProfScope ps(ctx, BFHE_K_NTT_INV, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
-    ntt_config((int)ctx->logN, &log_m, &log_e);
+    ntt_config((int)ctx->logN, 1, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, mont);
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
-    const bool full = subs == 1;
     if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
-    int rc = [&]() -> int {
-        INV_CASE(10, 3) INV_CASE(10, 4) INV_CASE(10, 5)
-        INV_CASE(11, 3) INV_CASE(11, 4) INV_CASE(11, 5)
-        INV_CASE(12, 3) INV_CASE(12, 4) INV_CASE(12, 5)
-        INV_CASE(13, 3) INV_CASE(13, 4) INV_CASE(13, 5)
-        INV_CASE(14, 4) INV_CASE(14, 5)
-        return set_error(BFHE_EINVAL, "no NTT configuration for this ring degree");
-    }();
-    if (rc != BFHE_OK || full) return rc;
-    k_ntt_inv_top<<<dim3(blocks, 8), 256, 0, st>>>(a);
-    BFHE_LAUNCH_CHECK("k_ntt_inv_top");
-    return BFHE_OK;
+    const bool split = subs == 2;
+    INV_CASE(10, 3) INV_CASE(10, 4) INV_CASE(10, 5)
+    INV_CASE(11, 3) INV_CASE(11, 4) INV_CASE(11, 5)
+    INV_CASE(12, 3) INV_CASE(12, 4) INV_CASE(12, 5)
+    INV_CASE(13, 3) INV_CASE(13, 4) INV_CASE(13, 5)
+    INV_CASE(14, 4) INV_CASE(14, 5)
+    return set_error(BFHE_EINVAL, "no NTT configuration for this ring degree");
 }

@@ -24,6 +24,8 @@ SMALL = dict(N=1024, L=3, alpha=1)         # odd limb count, ragged vs. template
 ALPHA2 = dict(N=1024, L=4, alpha=2)        # two special primes (mod-down by a 2-prime CRT)
 WIDE = dict(N=32768, L=2, alpha=2)         # N = 32768: the two-pass NTT path
 LOW_T = dict(N=1024, L=2, alpha=1, t=12289)  # t - 1 = 3 * 2^12: pow with an odd step
+MID = dict(N=16384, L=2, alpha=1)          # N = 16384: split-half forward NTT, whole-limb inverse
+C4 = dict(N=16384, L=8, alpha=1)           # the benchmark's parameters
 
 
 class Pair:
@@ -67,7 +69,7 @@ def test_params_and_keys(name, cfg):
     assert np.array_equal(rlk.cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("name,cfg", [("C1", C1), ("WIDE", WIDE)])
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("WIDE", WIDE), ("MID", MID)])
 def test_ntt_convolution(name, cfg):
     """INTT(NTT(a) . NTT(b)) equals the exact negacyclic product mod q; INTT(NTT(a)) = a."""
     from oracle.poly import negacyclic
@@ -130,7 +132,7 @@ def test_linear_ops():
 
 
 @pytest.mark.parametrize("name,cfg,n", [("C1", C1, 3), ("SMALL", SMALL, 2), ("ALPHA2", ALPHA2, 2),
-                                        ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2)])
+                                        ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2), ("MID", MID, 1)])
 def test_mul_relin(name, cfg, n):
     P = pair(name, cfg)
     prm = P.prm
@@ -249,3 +251,22 @@ def test_square_path(name, cfg):
     d = cts_to_device(prm, xs)
     got = P.ctx.mul_relin(d, d)
     assert_ct_equal(prm, got, [bfv.mul_relin(prm, P.keys, x, x) for x in xs], "square")
+
+
+def test_mul_relin_at_benchmark_parameters():
+    """N = 16384, L = 8, alpha = 1 (the bench's ring): keys, one mul_relin and one squaring, bit for bit.
+    The oracle takes about a minute here."""
+    P = pair("C4", C4)
+    prm = P.prm
+    sk, pk, _ = P.ctx.export_keys()
+    assert sk.cpu().numpy().tolist() == P.keys.s
+    assert np.array_equal(pk.cpu().numpy(), ct_to_rns(prm, (P.keys.pk0, P.keys.pk1)))
+    y = inputs.slots(20, 2, prm.N, hi=prm.t)
+    ct = P.ctx.encrypt(torch.from_numpy(y).cuda(), seed=121)
+    a, b = P.enc(y[0], 121, 0), P.enc(y[1], 121, 1)
+    assert_ct_equal(prm, ct, [a, b], "encrypt C4")
+    got = P.ctx.mul_relin(ct[0:1].contiguous(), ct[1:2].contiguous())
+    assert_ct_equal(prm, got, [bfv.mul_relin(prm, P.keys, a, b)], "mul_relin C4")
+    sq = P.ctx.mul_relin(got, got)
+    p = (y[0] * y[1]) % prm.t
+    assert np.array_equal(P.ctx.decrypt(sq).cpu().numpy()[0], (p * p) % prm.t)
