@@ -212,6 +212,14 @@ int bfhe_op_counts(bfhe_ctx* ctx, uint64_t out[4], int reset);
  * evaluation order, inverse maps back (inputs canonical). */
 int bfhe_ntt(bfhe_ctx* ctx, uint64_t* data, size_t n_polys, uint32_t n_limbs, int inverse, void* stream);
 
+/* NTT block shape for ring degree 2^logN and one direction (inverse != 0): a
+ * CTA transforms 2^log_m words (log_m = logN, or logN - 1 with the limb split
+ * over two CTAs), each thread holding 2^log_e of them.  log_m = 0 only reads
+ * the current shape into *cur_m, *cur_e (may be NULL).  Process-wide; used
+ * by the autotuner.  Shapes: log_m in [10, 14], log_e in [3, 5] (>= 4 at
+ * log_m = 14). */
+int bfhe_ntt_config(uint32_t logN, int inverse, uint32_t log_m, uint32_t log_e, uint32_t* cur_m, uint32_t* cur_e);
+
 /* Measurement support.  While profiling is on, every launch of the kernel
  * classes below is bracketed by CUDA events on its own stream;
  * bfhe_profile_read synchronises on the last event and returns, per class,

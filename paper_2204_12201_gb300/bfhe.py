@@ -66,6 +66,7 @@ def load():
         "bfhe_profile_read": (I, [P, P, P, P]),
         "bfhe_probe_modmul": (I, [I, U32, P, P]),
         "bfhe_launch_count": (ctypes.c_uint64, []),
+        "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
         "bfhe_last_error": (ctypes.c_char_p, []),
     }
@@ -269,3 +270,10 @@ def probe_modmul(device=0, iters=1 << 14):
 def launch_count():
     """Kernels launched by the library so far in this process."""
     return int(load().bfhe_launch_count())
+
+
+def ntt_config(logN, inverse, log_m=0, log_e=0):
+    """Set (log_m != 0) and return the NTT block shape (log_m, log_e) for ring degree 2^logN."""
+    m, e = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().bfhe_ntt_config(logN, int(inverse), log_m, log_e, ctypes.byref(m), ctypes.byref(e)))
+    return m.value, e.value

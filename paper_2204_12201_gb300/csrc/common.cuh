@@ -109,8 +109,8 @@ struct PrimeTab {
     const u64* qinv;     // -q^-1 mod 2^64
     const u64* mu;       // floor(2^64 / q)
     const u64* tw;       // [nP][N][2] (psi^brv(k), Shoup companion)      forward twiddles
-    const u64* itw;      // [nP][N][2] (psi^-brv(k), Shoup companion)     inverse twiddles
-    const u64* fin;      // [nP][8]: inverse last-stage constants (w, ws) x {ninv, ninv*itw[1]} x {plain, Montgomery}
+    const u64* itw;      // [nP][N][2] inverse (DIT) twiddles: entry 2^b + j = omega^-(N/2^(b+1)) j, omega = psi^2
+    const u64* twist;    // [nP][2][N][2] output twist N^-1 psi^-m (plain; times 2^64 mod q)
 };
 
 // limb -> prime index map of a polynomial base: limb < split ? limb : limb + off

@@ -409,8 +409,8 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
 
     // per-prime tables
     Arena ar;
-    std::vector<u64> qv(c->primes), qinv(nP), mu(nP), R2(nP), fin(nP * 8);
-    std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2);
+    std::vector<u64> qv(c->primes), qinv(nP), mu(nP), R2(nP);
+    std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2), twist((size_t)nP * 2 * N * 2);
     for (uint32_t p = 0; p < nP; ++p) {
         const u64 q = c->primes[p];
         u64 x = q;   // Newton: q * x = 1 mod 2^64
@@ -421,28 +421,43 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
         R2[p] = mulmod(R, R, q);
         const u64 psi = (p == nP - 1) ? powmod(least_primitive_root(q), (q - 1) / (2 * (u64)N), q) : root_2n(q, N);
         const u64 ipsi = invmod(psi, q);
-        // psi^brv(k), psi^-brv(k)
-        std::vector<u64> pw(N), ipw(N);
+        // powers psi^k and psi^-k, k < 2N
+        std::vector<u64> pw(2 * N), ipw(2 * N);
         pw[0] = ipw[0] = 1;
-        for (uint32_t k = 1; k < N; ++k) {
+        for (uint32_t k = 1; k < 2 * N; ++k) {
             pw[k] = mulmod(pw[k - 1], psi, q);
             ipw[k] = mulmod(ipw[k - 1], ipsi, q);
         }
+        // forward: psi^brv(k)
         for (uint32_t k = 0; k < N; ++k) {
             const size_t o = ((size_t)p * N + k) * 2;
             tw[o] = pw[c->brv[k]];
             tw[o + 1] = shoup_of(tw[o], q);
-            itw[o] = ipw[c->brv[k]];
-            itw[o + 1] = shoup_of(itw[o], q);
         }
+        // inverse DIT: entry 2^b + j (j < 2^b) = omega^-((N >> (b+1)) j) = psi^-(2 (N >> (b+1)) j)
+        itw[(size_t)p * N * 2] = 1;
+        itw[(size_t)p * N * 2 + 1] = shoup_of(1, q);
+        for (uint32_t b = 0; (1u << b) < N; ++b) {
+            for (uint32_t j = 0; j < (1u << b); ++j) {
+                const size_t o = ((size_t)p * N + (1u << b) + j) * 2;
+                const u64 e = (2ull * (N >> (b + 1)) * j) % (2ull * N);
+                itw[o] = ipw[e];
+                itw[o + 1] = shoup_of(itw[o], q);
+            }
+        }
+        // twist N^-1 psi^-m, plain and times R
         const u64 ninv = invmod(N % q, q);
-        const u64 w1 = mulmod(ninv, itw[((size_t)p * N + 1) * 2], q);
-        const u64 ninvR = mulmod(ninv, R, q), w1R = mulmod(w1, R, q);
-        const u64 f[8] = {ninv, shoup_of(ninv, q), w1, shoup_of(w1, q), ninvR, shoup_of(ninvR, q), w1R, shoup_of(w1R, q)};
-        for (int i = 0; i < 8; ++i) fin[p * 8 + i] = f[i];
+        for (uint32_t m = 0; m < N; ++m) {
+            const u64 v0 = mulmod(ninv, ipw[m], q), v1 = mulmod(v0, R, q);
+            const size_t o0 = (((size_t)p * 2 + 0) * N + m) * 2, o1 = (((size_t)p * 2 + 1) * N + m) * 2;
+            twist[o0] = v0;
+            twist[o0 + 1] = shoup_of(v0, q);
+            twist[o1] = v1;
+            twist[o1 + 1] = shoup_of(v1, q);
+        }
     }
-    const size_t o_q = ar.add(qv), o_qinv = ar.add(qinv), o_mu = ar.add(mu), o_R2 = ar.add(R2), o_fin = ar.add(fin);
-    const size_t o_tw = ar.add(tw), o_itw = ar.add(itw);
+    const size_t o_q = ar.add(qv), o_qinv = ar.add(qinv), o_mu = ar.add(mu), o_R2 = ar.add(R2);
+    const size_t o_tw = ar.add(tw), o_itw = ar.add(itw), o_twist = ar.add(twist);
     std::vector<u64> brv_packed((N + 1) / 2);
     for (uint32_t k = 0; k < N; k += 2)
         brv_packed[k / 2] = (u64)c->brv[k] | ((u64)(k + 1 < N ? c->brv[k + 1] : 0) << 32);
@@ -498,7 +513,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->tab.mu = base + o_mu;
     c->tab.tw = base + o_tw;
     c->tab.itw = base + o_itw;
-    c->tab.fin = base + o_fin;
+    c->tab.twist = base + o_twist;
     c->d_R2 = base + o_R2;
     c->d_brv = (uint32_t*)(base + o_brv);
     c->ext_QB = ext_ptrs(base, eQB);

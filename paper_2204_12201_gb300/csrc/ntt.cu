@@ -7,11 +7,12 @@
 // quotient estimate may be one short, see shoup_lazy3), grows the bound by 3q
 // per stage and is never reduced in between: from inputs < 4q, 15 stages stay
 // below 49q < 2^56 for q < 2^50, and one Barrett-style reduction at the end
-// makes the output canonical.  Inverse: Gentleman-Sande with psi^-brv
-// twiddles and exact Shoup products, values in [0, 2q) (X + Y reduced by an
-// unsigned min), the N^-1 scale (times R = 2^64 when the inputs carry a
-// Montgomery factor) merged into the last stage.  Twiddles are stored as
-// (w, Shoup(w)) pairs and fetched as one 16-byte load.
+// makes the output canonical.  Inverse: a_m = N^-1 psi^-m sum_k a^_k
+// omega^-km (omega = psi^2) -- a cyclic decimation-in-time transform on the
+// bit-reversed input with the same reduction-free butterfly, then one twist
+// product by N^-1 psi^-m per word (times R = 2^64 when the inputs carry a
+// Montgomery factor), which also makes the output canonical.  Twiddles are
+// stored as (w, Shoup(w)) pairs and fetched as one 16-byte load.
 //
 // One CTA transforms a block of M = 2^LOG_M words of a limb held in shared
 // memory; each thread keeps E = 2^LOG_E words in registers and runs up to
@@ -28,8 +29,8 @@
 // keeps the output of its own half, so the stage costs no extra pass.
 // Inverse: the two CTAs form a thread-block cluster; after the inner stages
 // each publishes its half in shared memory, reads the partner's through
-// distributed shared memory and finishes the outermost stage (with the N^-1
-// scale) for its own half.
+// distributed shared memory and finishes the outermost stage (and the twist)
+// for its own half.
 #include <cooperative_groups.h>
 
 #include <cstdlib>
@@ -157,55 +158,42 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 ? 2 : 1)) k_
 }
 
 // ---------------------------------------------------------------- inverse stages
-__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
-
-template <int LOG_E, int W_LO, int LO, int HI, bool SCALE_TOP>
-__device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ itw, u64 q,
-                                           const u64* fin) {
+// Decimation in time on the bit-reversed input with inverse roots: the butterfly on
+// bit b at lower index x is (U, V) -> (U + T, U - T + 3q), T = V omega^-(N/2^(b+1)) (x mod 2^b)
+// (table entry 2^b + (x mod 2^b)); bounds grow by 3q per stage, as in the forward.
+// The natural-order output is then multiplied by the twist N^-1 psi^-m.
+template <int LOG_E, int W_LO, int LO, int HI>
+__device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const ulonglong2* __restrict__ itw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q2 = q << 1;
+    const u64 q3 = 3 * q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = LO + st;
         const int h = b - W_LO;
-        const u64 base = jb >> (b + 1);
-        if (SCALE_TOP && b == HI) {
-            const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
+        const int tbase = (1 << b) + (base & ((1 << b) - 1));
+#pragma unroll
+        for (int r = 0; r < (1 << h); ++r) {
+            const ulonglong2 wp = __ldg(itw + tbase + (r << W_LO));
 #pragma unroll
             for (int g = 0; g < (E >> (h + 1)); ++g) {
-#pragma unroll
-                for (int r = 0; r < (1 << h); ++r) {
-                    const int e = (g << (h + 1)) | r;
-                    const int e2 = e | (1 << h);
-                    const u64 X = x[e], Y = x[e2];
-                    x[e] = shoup(X + Y, n0, n0s, q);
-                    x[e2] = shoup(X + q2 - Y, n1, n1s, q);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int g = 0; g < (E >> (h + 1)); ++g) {
-                const ulonglong2 wp = __ldg(itw + base + g);
-#pragma unroll
-                for (int r = 0; r < (1 << h); ++r) {
-                    const int e = (g << (h + 1)) | r;
-                    const int e2 = e | (1 << h);
-                    const u64 X = x[e], Y = x[e2];
-                    const u64 S = X + Y;
-                    x[e] = umin64(S, S - q2);
-                    x[e2] = shoup_lazy(X + q2 - Y, wp.x, wp.y, q);
-                }
+                const int e = (g << (h + 1)) | r;
+                const int e2 = e | (1 << h);
+                const u64 U = x[e];
+                const u64 T = shoup_lazy3(x[e2], wp.x, wp.y, q);
+                x[e] = U + T;
+                x[e2] = U + q3 - T;
             }
         }
     }
 }
 
-// MODE 1: the block is the whole limb (scale in the last stage); MODE 2: half `half`
-// of a limb of N = 2M words, finished through the partner CTA of the cluster.
+// MODE 1: the block is the whole limb; MODE 2: half `half` of a limb of N = 2M words,
+// whose outermost stage pairs with the partner CTA of the cluster.
 template <int LOG_M, int LOG_E, int P, int MODE>
-__device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* itw,
-                                         u64 q, const u64* fin, const u64* in, u64* out, int half) {
+__device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, const ulonglong2* itw,
+                                         const ulonglong2* twist, u64 q, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
+    constexpr int M = 1 << LOG_M;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
     constexpr int LO = P * LOG_E;
     constexpr int HI = (LO + LOG_E - 1) < (LOG_M - 1) ? (LO + LOG_E - 1) : (LOG_M - 1);
@@ -225,31 +213,40 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
     }
     constexpr bool LAST = (P + 1 == NPASS);
-    inv_stages<LOG_E, W_LO, LO, HI, MODE == 1 && LAST>(x, jglob + base, itw, q, fin);
+    inv_stages<LOG_E, W_LO, LO, HI>(x, base, itw, q);
     if constexpr (!LAST) {
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         __syncthreads();
-        inv_pass<LOG_M, LOG_E, P + 1, MODE>(x, sm, tid, jglob, itw, q, fin, in, out, half);
+        inv_pass<LOG_M, LOG_E, P + 1, MODE>(x, sm, tid, itw, twist, q, in, out, half);
     } else if constexpr (MODE == 2) {
-        // outermost stage across the two halves: publish, then read the partner's words
-        // at the same block positions through distributed shared memory
+        // outermost stage across the halves: publish, read the partner's words at the same
+        // block positions through distributed shared memory, finish, twist
         cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         cl.sync();
         const u64* peer = cl.map_shared_rank(sm, cl.block_rank() ^ 1u);
-        const u64 q2 = q << 1;
-        const u64 n0 = fin[0], n0s = fin[1], n1 = fin[2], n1s = fin[3];
+        const u64 q3 = 3 * q;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const u64 mine = x[e], other = peer[phys(base + (e << W_LO))];
-            out[base + (e << W_LO)] = half ? shoup(other + q2 - mine, n1, n1s, q) : shoup(mine + other, n0, n0s, q);
+            const int j = base + (e << W_LO);
+            const u64 other = peer[phys(j)];
+            const u64 U = half ? other : x[e], V = half ? x[e] : other;
+            const ulonglong2 wp = __ldg(itw + M + j);
+            const u64 T = shoup_lazy3(V, wp.x, wp.y, q);
+            const u64 y = half ? U + q3 - T : U + T;
+            const ulonglong2 tw = __ldg(twist + j + half * M);
+            out[j] = shoup(y, tw.x, tw.y, q);
         }
         cl.sync();   // the partner has finished reading this CTA's shared memory
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) out[base + (e << W_LO)] = x[e];
+        for (int e = 0; e < E; ++e) {
+            const int j = base + (e << W_LO);
+            const ulonglong2 tw = __ldg(twist + j);
+            out[j] = shoup(x[e], tw.x, tw.y, q);
+        }
     }
 }
 
@@ -260,10 +257,9 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14
     const int half = blockIdx.y;
     const u64 q = a.tab.q[lp.p];
     const ulonglong2* itw = reinterpret_cast<const ulonglong2*>(a.tab.itw) + (size_t)lp.p * a.N;
-    const u64* fin = a.tab.fin + (size_t)lp.p * 8 + (a.mont ? 4 : 0);
-    const u64 jglob = (u64)a.N + ((u64)half << LOG_M);
+    const ulonglong2* twist = reinterpret_cast<const ulonglong2*>(a.tab.twist) + ((size_t)lp.p * 2 + (a.mont ? 1 : 0)) * a.N;
     u64 x[1 << LOG_E];
-    inv_pass<LOG_M, LOG_E, 0, MODE>(x, sm, threadIdx.x, jglob, itw, q, fin, lp.in + ((size_t)half << LOG_M),
+    inv_pass<LOG_M, LOG_E, 0, MODE>(x, sm, threadIdx.x, itw, twist, q, lp.in + ((size_t)half << LOG_M),
                                     lp.out + ((size_t)half << LOG_M), half);
 }
 
@@ -351,10 +347,12 @@ int env_int(const char* name) {
 
 void ntt_set_log_e(int log_e) { g_log_e_override = log_e; }
 
-// Block size and registers per thread (measured on GB300): N <= 8192 in one
-// block; N = 16384 forward as two 8192-word halves (two CTAs per SM), inverse
-// in one block; N = 32768 as two 16384-word halves.  BFHE_NTT_LOG_M /
-// BFHE_NTT_LOG_E override (tuning).
+// Block size and registers per thread.  Defaults (measured on GB300): N <= 8192
+// in one block; N = 16384 forward as two 8192-word halves (two CTAs per SM) and
+// inverse in one block; N = 32768 as two 16384-word halves.  bfhe_ntt_config
+// (the autotuner) or BFHE_NTT_LOG_M / BFHE_NTT_LOG_E override them.
+int g_cfg[16][2][2] = {};   // [logN][inverse] -> (log_m, log_e), 0 = default
+
 int ntt_config(int logN, int inverse, int* log_m, int* log_e) {
     static const int env_m = env_int("BFHE_NTT_LOG_M");
     static const int env_e = env_int("BFHE_NTT_LOG_E");
@@ -364,9 +362,30 @@ int ntt_config(int logN, int inverse, int* log_m, int* log_e) {
     int e = (m == 14 || (m == 13 && logN == 14)) ? 5 : 4;
     if (env_e >= 3 && env_e <= 5) e = env_e;
     if (g_log_e_override >= 3 && g_log_e_override <= 5) e = g_log_e_override;
+    if (logN >= 0 && logN < 16 && g_cfg[logN][inverse ? 1 : 0][0]) {
+        m = g_cfg[logN][inverse ? 1 : 0][0];
+        e = g_cfg[logN][inverse ? 1 : 0][1];
+    }
     if (m == 14 && e < 4) e = 4;
     *log_m = m;
     *log_e = e;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_ntt_config(uint32_t logN, int inverse, uint32_t log_m, uint32_t log_e, uint32_t* cur_m,
+                               uint32_t* cur_e) {
+    if (logN < 10 || logN > 15) return set_error(BFHE_EINVAL, "logN must be in [10, 15]");
+    if (log_m != 0) {
+        if (log_m > logN || log_m + 1 < logN || log_m < 10 || log_m > 14 || log_e < 3 || log_e > 5 ||
+            (log_m == 14 && log_e < 4))
+            return set_error(BFHE_EINVAL, "unsupported NTT block configuration");
+        g_cfg[logN][inverse ? 1 : 0][0] = (int)log_m;
+        g_cfg[logN][inverse ? 1 : 0][1] = (int)log_e;
+    }
+    int m, e;
+    ntt_config((int)logN, inverse, &m, &e);
+    if (cur_m) *cur_m = (uint32_t)m;
+    if (cur_e) *cur_e = (uint32_t)e;
     return BFHE_OK;
 }
 
