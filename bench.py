@@ -99,51 +99,6 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def genotype_inputs(seed):
-    from paper_2204_12201_gb300 import inputs
-    N = WL["N"]
-    used = N_IND * N_TARGETS
-    G = inputs.genotypes(seed, N_IND, N_TARGETS, N_TAGS)                 # [32][16000]
-    W = inputs.weights(seed + 1, N_CLASSES, N_TAGS, N_TARGETS, N_IND)     # [3][32][16000]
-    import numpy as np
-    Gs = np.zeros((N_TAGS, N), dtype=np.int64)
-    Ws = np.zeros((N_CLASSES, N_TAGS, N), dtype=np.int64)
-    Gs[:, :used] = G
-    Ws[:, :, :used] = W
-    return Gs, Ws
-
-
-# --------------------------------------------------------------------------- the job
-class GenotypeJob:
-    def __init__(self, ctx, use_graph=False):
-        import torch
-        from paper_2204_12201_gb300 import circuits
-        self.torch = torch
-        self.ctx = ctx
-        net = circuits.Netlist()
-        s0, s1, s2 = net.inputs(S_BITS), net.inputs(S_BITS), net.inputs(S_BITS)
-        self.out_wires = net.argmax3(s0, s1, s2)
-        self.circ = circuits.Compiled(ctx, net, 1)
-        self.circuit_muls = net.n_mul
-
-    def run(self, G_dev, W_dev, seed):
-        torch, ctx = self.torch, self.ctx
-        N, L = ctx.N, ctx.L
-        g = ctx.encrypt(G_dev, seed)                                  # [32] tag ciphertexts
-        rep = g.repeat(N_CLASSES, 1, 1, 1)                            # [96]
-        x = ctx.mul_plain(rep, W_dev.view(N_CLASSES * N_TAGS, N))     # weighted tags
-        x = x.view(N_CLASSES, N_TAGS, 2, L, N)
-        while x.shape[1] > 1:                                         # sum over tags
-            h = x.shape[1] // 2
-            x = ctx.add(x[:, :h].contiguous(), x[:, h:].contiguous())
-        scores = x.view(N_CLASSES, 2, L, N)                           # SecureMod scores < 4096
-        bits = ctx.mod_to_bits(scores, S_BITS, 0, (1 << S_BITS) - 1)  # [12][3]
-        self.circ.set_inputs(bits.transpose(0, 1).reshape(N_CLASSES * S_BITS, 1, 2, L, N))
-        self.circ.run()
-        idx = self.circ.out(self.out_wires).view(2, 2, L, N)
-        return ctx.decrypt(idx)                                       # [2][N]: index bits per slot
-
-
 # --------------------------------------------------------------------------- CPU oracle leg
 def _oracle_mul_relin(args):
     """One oracle mul_relin on random ciphertexts and a random-key stand-in; returns seconds."""
@@ -310,17 +265,18 @@ def main():
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2204_12201_gb300 import bfhe, circuits
+    from paper_2204_12201_gb300 import autotune, bfhe, circuits, workloads
 
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    shapes = autotune.tune(ring_degrees=(8192, 16384))     # NTT block shapes for the rings used here
     ctx = bfhe.Context(N=WL["N"], L=WL["L"], alpha=WL["alpha"], t=WL["t"], device=local)
     ctx.keygen(1 + rank)
-    job = GenotypeJob(ctx)
-    Gs, Ws = genotype_inputs(1004 + rank)
+    job = workloads.GenotypeJob(ctx, n_tags=N_TAGS, s_bits=S_BITS)
+    Gs, Ws = workloads.genotype_inputs(1004 + rank, WL["N"], N_IND, N_TARGETS, N_TAGS, N_CLASSES)
     G_dev = torch.from_numpy(Gs).cuda()
     W_dev = torch.from_numpy(Ws).cuda()
     for w in range(args.warmup):
@@ -397,6 +353,7 @@ def main():
                 "config": {"workload": WORKLOAD, "N": WL["N"], "L": WL["L"], "alpha": WL["alpha"],
                            "t": WL["t"], "mul_relin_per_step": n_mul // args.steps,
                            "parallelism": "replicas" if world > 1 else "single",
+                           "ntt_shapes": {k: v["shape"] for k, v in shapes.items()},
                            "l2": "no flush: per-step working set > 10 GB >> 129 MB L2"},
                 "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu_line, "ops_per_step": {"add": n_add // args.steps, "sub": n_sub // args.steps,

@@ -10,8 +10,9 @@ Every gate equation of Sec. 3.1 is one MUL and one LIN (NOT is a LIN).
 Scheduling: a MUL sits one level above its deepest input; a LIN sits on the
 level of its deepest input and, inside a level, on a sub-level above the
 LINs it reads.  Level d runs as one bfhe_gate_level call holding all its
-MULs (one batched multiply) plus the LINs of sub-level 0, then one call per
-further LIN sub-level.  Tables are uploaded once; the whole circuit can be
+MULs (one batched multiply), then one call per LIN sub-level (a call may not
+read a wire that another entry of the same call writes, and the LINs of a
+level read its MULs).  Tables are uploaded once; the whole circuit can be
 captured in a CUDA graph and replayed.
 
 Netlists (the same structure the tests' oracle circuits follow):
@@ -183,10 +184,9 @@ class Compiled:
         self.ctx, self.net, self.n = ctx, net, n
         self.calls = []      # (table tensor, n_gates, n_mul)
         for _, muls, subs in net.schedule():
-            first = muls + (subs[0] if subs else [])
-            if first:
-                self.calls.append(self._table(first, len(muls)))
-            for s in subs[1:]:
+            if muls:
+                self.calls.append(self._table(muls, len(muls)))
+            for s in subs:
                 self.calls.append(self._table(s, 0))
         self.depth = sum(1 for c in self.calls if c[2] > 0)
         self.wires = torch.zeros(net.n_wires, n, 2, ctx.L, ctx.N, dtype=torch.int64, device=ctx.device)

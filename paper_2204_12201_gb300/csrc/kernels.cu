@@ -171,41 +171,38 @@ __global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, in
     }
 }
 
-// key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC)
-template <int CB>
-__global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int L, int QP, PrimeTab tab, int N) {
-    const size_t plane = (size_t)QP * N;   // one digit's limbs
-    const int nchunks = (n + CB - 1) / CB;
-    const size_t total = plane * nchunks;
+// key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC).
+// A thread owns one word (k, coefficient) of Q u P: it keeps the 2L key words of that word in
+// registers and walks a group of ciphertexts, so the key is read once per group.
+template <int L>
+__global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, int cpg, PrimeTab tab, int N) {
+    const size_t plane = (size_t)QP * N;
+    const int groups = (n + cpg - 1) / cpg;
+    const size_t total = plane * groups;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const size_t off = idx % plane;
-        const int chunk = (int)(idx / plane);
+        const int grp = (int)(idx / plane);
         const int k = (int)(off / N);
         const u64 q = tab.q[k], qinv = tab.qinv[k];
-        u64 h0[CB], l0[CB], h1[CB], l1[CB];
+        u64 k0[L], k1[L];
 #pragma unroll
-        for (int b = 0; b < CB; ++b) h0[b] = l0[b] = h1[b] = l1[b] = 0;
         for (int j = 0; j < L; ++j) {
-            const u64 k0 = rlk[((size_t)j * 2 + 0) * plane + off];
-            const u64 k1 = rlk[((size_t)j * 2 + 1) * plane + off];
-#pragma unroll
-            for (int b = 0; b < CB; ++b) {
-                const int c = chunk * CB + b;
-                if (c < n) {
-                    const u64 d = Dg[((size_t)c * L + j) * plane + off];
-                    mac128(h0[b], l0[b], d, k0);
-                    mac128(h1[b], l1[b], d, k1);
-                }
-            }
+            k0[j] = rlk[((size_t)j * 2 + 0) * plane + off];
+            k1[j] = rlk[((size_t)j * 2 + 1) * plane + off];
         }
+        const int c_end = min(n, (grp + 1) * cpg);
+        for (int c = grp * cpg; c < c_end; ++c) {
+            u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+            const u64* d = Dg + (size_t)c * L * plane + off;
 #pragma unroll
-        for (int b = 0; b < CB; ++b) {
-            const int c = chunk * CB + b;
-            if (c < n) {
-                W[((size_t)c * 2 + 0) * plane + off] = redc(h0[b], l0[b], q, qinv);
-                W[((size_t)c * 2 + 1) * plane + off] = redc(h1[b], l1[b], q, qinv);
+            for (int j = 0; j < L; ++j) {
+                const u64 v = d[(size_t)j * plane];
+                mac128(h0, l0, v, k0[j]);
+                mac128(h1, l1, v, k1[j]);
             }
+            W[((size_t)c * 2 + 0) * plane + off] = redc(h0, l0, q, qinv);
+            W[((size_t)c * 2 + 1) * plane + off] = redc(h1, l1, q, qinv);
         }
     }
 }
@@ -688,12 +685,12 @@ int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, int square, cudaStream_t s
     return BFHE_OK;
 }
 
-int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
-    ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
+template <int L>
+int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
     const int QP = (int)(ctx->L + ctx->alpha);
-    constexpr int CB = 4;
-    const size_t work = (size_t)QP * ctx->N * ((n + CB - 1) / CB);
-    LAUNCH(k_inner<CB>, work, Dg, ctx->d_rlk_ntt, W, n, (int)ctx->L, QP, ctx->tab, (int)ctx->N);
+    const int cpg = n < 4 ? 1 : (n + 3) / 4;   // four groups: enough threads, key read four times
+    const size_t work = (size_t)QP * ctx->N * ((n + cpg - 1) / cpg);
+    LAUNCH(k_inner<L>, work, Dg, ctx->d_rlk_ntt, W, n, QP, cpg, ctx->tab, (int)ctx->N);
     return BFHE_OK;
 }
 
@@ -740,6 +737,11 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
         case 16: return FN<16>(__VA_ARGS__);                                                                   \
         default: return set_error(BFHE_EINVAL, "unsupported number of data primes");                         \
     }
+
+int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
+    ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
+    SWITCH_L(ctx->L, run_inner, ctx, Dg, W, n, st)
+}
 
 int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const double L_ = ctx->L, K_ = ctx->K;

@@ -24,9 +24,12 @@
 // inverse: coalesced).
 //
 // When N = 2M a limb is split over two CTAs (so that two of them share an SM
-// at N = 16384).  Forward: the outermost stage pairs word j of the first half
+// at N = 16384), launched as a thread-block cluster of two so they are always
+// co-resident.  Forward: the outermost stage pairs word j of the first half
 // with word j of the second; each CTA reads both halves in its first pass and
-// keeps the output of its own half, so the stage costs no extra pass.
+// keeps the output of its own half, so the stage costs no extra pass; a
+// cluster barrier after those reads keeps an in-place transform from
+// overwriting words the partner has not read yet.
 // Inverse: the two CTAs form a thread-block cluster; after the inner stages
 // each publishes its half in shared memory, reads the partner's through
 // distributed shared memory and finishes the outermost stage (and the twist)
@@ -120,6 +123,8 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
                 const u64 T = shoup_lazy3(in[M + base + (e << W_LO)], w1.x, w1.y, q);
                 x[e] = half ? X + q3 - T : X + T;
             }
+            // both halves of the limb are read before either CTA writes (in-place transforms)
+            cg::this_cluster().sync();
         } else {
 #pragma unroll
             for (int e = 0; e < E; ++e) x[e] = in[base + (e << W_LO)];
@@ -280,8 +285,25 @@ int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
                                        (int)smem));
         attr = true;
     }
-    k_ntt_fwd<LOG_M, LOG_E, TOP><<<dim3(blocks, TOP ? 2 : 1), T, smem, st>>>(a);
-    BFHE_LAUNCH_CHECK("k_ntt_fwd");
+    if (TOP) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks, 2, 1);
+        cfg.blockDim = dim3(T, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = 2;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_fwd<LOG_M, LOG_E, TOP>, a));
+        BFHE_LAUNCH_CHECK("k_ntt_fwd (cluster)");
+    } else {
+        k_ntt_fwd<LOG_M, LOG_E, TOP><<<dim3(blocks, 1), T, smem, st>>>(a);
+        BFHE_LAUNCH_CHECK("k_ntt_fwd");
+    }
     return BFHE_OK;
 }
 
