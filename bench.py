@@ -12,7 +12,9 @@ bits, and decryption of the two index bits.  The metric counts the
 relinearised ciphertext multiplies the step performs (op counter) per
 second.  Extra keys report the batched-vs-per-op mul_relin rate at
 N = 16384, bit-gates/s of the 16-bit comparator and 16x16 multiplier
-circuits at N = 8192 (eager and CUDA-graph), and the modmul probe.
+circuits at N = 8192 (eager and CUDA-graph), the modmul probe, and the
+serving loop's p50/p99 latency and throughput against one-request-at-a-time
+per-op launches at two arrival rates.
 
 --impl reference times the CPU oracle (the plain arbitrary-precision BFV the
 library is checked against) on the host cores instead.
@@ -232,6 +234,15 @@ def extras(torch, bfhe, circuits, ctx16):
         del comp
     ctx8.close()
     out["modmul_probe_per_s"] = bfhe.probe_modmul(torch.cuda.current_device())
+    # serving: a Poisson stream of mixed requests (N in {4096, 8192, 16384}, 1..16 squarings,
+    # 1..64 ciphertexts), continuous batching vs one request at a time with per-op launches
+    from paper_2204_12201_gb300 import serving
+    sv = {}
+    for rate in (20.0, 200.0):
+        r = serving.demo(n_req=60, rate=rate, seed=11)
+        sv["rate_%d" % int(rate)] = {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                                     for k, v in r.items() if isinstance(v, dict)}
+    out["serving"] = sv
     return {k: (round(v, 1) if isinstance(v, float) else v) for k, v in out.items()}
 
 
