@@ -181,7 +181,7 @@ class Server:
             if not progressed and pending:
                 wait = pending[0].arrival - (clock() - t0)
                 if wait > 0:
-                    sleep(min(wait, 0.002))
+                    sleep(max(0.0, min(wait, 0.002)))
                 elif self.used + self.need(pending[0]) > self.budget:
                     # memory-bound: wait for a completion
                     for r in finished:
@@ -204,7 +204,7 @@ def serve_sequential(backend, requests, clock=time.perf_counter, sleep=time.slee
     out = []
     for r in sorted(requests, key=lambda r: r.arrival):
         while clock() - t0 < r.arrival:
-            sleep(min(0.002, r.arrival - (clock() - t0)))
+            sleep(max(0.0, min(0.002, r.arrival - (clock() - t0))))
         r.t_admit = clock() - t0
         x = backend.encrypt(r)
         cts = [x[i:i + 1] for i in range(r.n)]
