@@ -12,7 +12,15 @@ Test infrastructure only.  Follows the paper directly:
   multiplies;
 * SecureMod -> SecureUint (Sec. 3.2.3, Eq. 2 and Listing 8): for each
   candidate c, eq_c = 1 - (x - c)^(t-1), then SecureUint(c) * SecureBool(eq_c)
-  and a per-bit sum over c.
+  and a per-bit sum over c;
+* SecureInt -> SecureMod (Sec. 3.2.2, Eq. 1, Listing 6): a multiplexer on the
+  sign bit between the Horner value and t - 2^s plus it (2 multiplies);
+* SecureMod -> SecureInt (Sec. 3.2.4, Listing 9): two SecureMod -> SecureUint
+  conversions (of x and of 2^s - t + x) and a per-bit multiplexer on the sign
+  bit of the first; Listing 9 names the width `s`, read as Size, and Eq. 3 and
+  the listing differ (a bit-level addition against a second conversion): the
+  listing is followed.  Its multiplexer over s bits costs 2s multiplies where
+  the paper's count says 2 (it counts the SecureInt product as one).
 
 Readings (the paper is silent or loose here):
 * constants are trivial ciphertexts (Delta [c]_t, 0);
@@ -131,8 +139,29 @@ class Evaluator:
                 else:
                     continue
                 bits[k] = term if bits[k] is None else self.add(bits[k], term)
-        zero = ([0] * self.prm.N, [0] * self.prm.N)
-        return [b if b is not None else zero for b in bits]
+        return [b if b is not None else self.trivial(0) for b in bits]
+
+    # -- Sec. 3.2.2, Eq. 1, Listing 6: SecureInt<s> -> SecureMod
+    def sint_to_mod(self, v):
+        """pos = Horner(v); neg = (t - 2^s) + pos; isNeg = v[s-1];
+        result = isNeg * neg + (1 - isNeg) * pos (needs t >= 2^s)."""
+        s = len(v)
+        pos = self.bits_to_mod(v)
+        neg = self.add_const(pos, (self.prm.t - (1 << s)) % self.prm.t)
+        is_neg = v[s - 1]
+        return self.add(self.mul(is_neg, neg), self.mul(self.const_sub(1, is_neg), pos))
+
+    # -- Sec. 3.2.4, Eq. 3, Listing 9: SecureMod -> SecureInt<s>
+    def mod_to_sint(self, x, s, cands_pos, cands_neg, mode=PAPER):
+        """pos = to_SecureUint(x); neg = to_SecureUint((2^s - t) + x); isNeg = pos[s-1];
+        result bit k = isNeg * neg[k] + (1 - isNeg) * pos[k] (needs 2^s >= t).
+        The two candidate ranges of the conversions are arguments (the listing scans all of Z_t)."""
+        t = self.prm.t
+        pos = self.mod_to_bits(x, s, cands_pos, mode)
+        neg = self.mod_to_bits(self.add_const(x, ((1 << s) - t) % t), s, cands_neg, mode)
+        is_neg = pos[s - 1]
+        not_neg = self.const_sub(1, is_neg)
+        return [self.add(self.mul(is_neg, neg[k]), self.mul(not_neg, pos[k])) for k in range(s)]
 
 
 def pow_mul_count(e):

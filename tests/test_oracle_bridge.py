@@ -10,6 +10,7 @@ logic is what is pinned there; noise is not involved).
 
 import itertools
 import random
+import types
 
 import pytest
 
@@ -33,6 +34,7 @@ class PlainEvaluator:
 
     def __init__(self, t, n):
         self.t, self.n = t, n
+        self.prm = types.SimpleNamespace(t=t, N=n)
         self.n_add = self.n_sub = self.n_mul = 0
 
     def add(self, a, b):
@@ -65,6 +67,10 @@ class PlainEvaluator:
     gate = bridge.Evaluator.gate
     bits_to_mod = bridge.Evaluator.bits_to_mod
     pow = bridge.Evaluator.pow
+    equality = bridge.Evaluator.equality
+    mod_to_bits = bridge.Evaluator.mod_to_bits
+    sint_to_mod = bridge.Evaluator.sint_to_mod
+    mod_to_sint = bridge.Evaluator.mod_to_sint
 
 
 TRUTH = {AND: lambda x, y, z: x & y, OR: lambda x, y, z: x | y, XOR: lambda x, y, z: x ^ y,
@@ -228,3 +234,76 @@ def test_adder_and_comparator_encrypted(tiny):
     assert _val([bfv.decrypt(prm, keys, c) for c in s]) == [x + y for x, y in zip(a, b)]
     lt = circuits.less_than(ev, ab, bb)
     assert bfv.decrypt(prm, keys, lt) == [int(x < y) for x, y in zip(a, b)]
+
+
+# ------------------------------------------------------------ signed conversions (Listings 6 and 9)
+@pytest.mark.parametrize("s", [2, 4, 8, 16])
+def test_sint_to_mod_all_values_plain(s):
+    """Eq. 1: a negative s-bit value v maps to t - 2^s + (two's complement bits) = v mod t."""
+    t = 65537
+    vals = list(range(-(1 << (s - 1)), 1 << (s - 1)))
+    if len(vals) > 4096:
+        vals = random.Random(s).sample(vals, 4096) + [-(1 << (s - 1)), -1, 0, (1 << (s - 1)) - 1]
+    ev = PlainEvaluator(t, len(vals))
+    bits = [[((v + (1 << s)) >> k) & 1 for v in vals] for k in range(s)]
+    r = ev.sint_to_mod(bits)
+    assert r == [v % t for v in vals]
+    # 2 multiplies and 2s + 1 additions or subtractions (Sec. 3.2.2)
+    assert ev.n_mul == 2 and ev.n_add + ev.n_sub == 2 * s + 1
+
+
+def test_sint_to_mod_encrypted(tiny):
+    prm, keys = tiny
+    s = 4                                         # t = 17 >= 2^4
+    vals = list(range(-8, 8))
+    ev = bridge.Evaluator(prm, keys)
+    for half in (vals[:8], vals[8:]):
+        bits = [bfv.encrypt(prm, keys, [((v + 16) >> k) & 1 for v in half], 81, k) for k in range(s)]
+        r = ev.sint_to_mod(bits)
+        assert bfv.decrypt(prm, keys, r) == [v % prm.t for v in half]
+
+
+def test_mod_to_sint_listing_arithmetic_plain():
+    """Listing 9 as printed, at t = 17, s = 5 (2^s >= t): values below 2^(s-1) come back as
+    their bits; x = 16 (read as -1) comes back as the bits of (2^s - t + x) mod t = 14, because
+    the listing's second conversion works mod t (Eq. 3 adds 2^s - t in bit-level arithmetic)."""
+    t, s = 17, 5
+    xs = list(range(t))
+    ev = PlainEvaluator(t, t)
+    out = ev.mod_to_sint(xs, s, range(t), range(t), SELECT)
+    got = _val(out)
+    assert got[:16] == list(range(16))
+    assert got[16] == ((1 << s) - t + 16) % t == 14
+    # two conversions (4 multiplies per candidate in the Fermat chain at t = 17), 2s for the multiplexer
+    assert ev.n_mul == 2 * t * 4 + 2 * s
+
+
+def test_mod_to_sint_encrypted_matches_plain(tiny):
+    prm, keys = tiny
+    s = 5
+    xs = [0, 3, 15, 16, 9, 12, 1, 7]
+    x = bfv.encrypt(prm, keys, xs, 91, 0)
+    ev = bridge.Evaluator(prm, keys)
+    bits = ev.mod_to_sint(x, s, range(prm.t), range(prm.t), SELECT)
+    want = [v if v < 16 else ((1 << s) - prm.t + v) % prm.t for v in xs]
+    assert _val([bfv.decrypt(prm, keys, b) for b in bits]) == want
+    assert ev.n_mul == 2 * prm.t * 4 + 2 * s
+
+
+@pytest.mark.parametrize("t,s", [(17, 5), (97, 7), (257, 9), (257, 10)])
+def test_mod_to_sint_against_eq3(t, s):
+    """Eq. 3 (bit-level: Y = X when X_{s-1} = 0, else the s-bit sum 2^s - t + X) is the two's
+    complement of x - t for x >= 2^(s-1) and of x otherwise.  The listing agrees with it on every
+    x whose shifted value 2^s - t + x stays below t, and on every non-negative x; elsewhere its
+    mod-t addition wraps (the case the listing does not cover)."""
+    xs = list(range(t))
+    ev = PlainEvaluator(t, t)
+    got = _val(ev.mod_to_sint(xs, s, range(t), range(t), SELECT))
+    for x, g in zip(xs, got):
+        eq3 = x if x < (1 << (s - 1)) else ((1 << s) - t + x) % (1 << s)
+        if x < (1 << (s - 1)) or (1 << s) - t + x < t:
+            assert g == eq3, x
+            v = eq3 - (1 << s) if eq3 >> (s - 1) else eq3
+            assert v % t == x                     # the signed value is congruent to x
+        else:
+            assert g == ((1 << s) - t + x) % t, x
