@@ -170,6 +170,31 @@ enum { BFHE_PAPER = 0, BFHE_SELECT = 1 };
 int bfhe_mod_to_bits(bfhe_ctx* ctx, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
                      uint64_t* bits_out, size_t n, void* stream);
 
+/* SecureInt<s> -> SecureMod (Sec. 3.2.2, Eq. 1, Listing 6): bits hold the
+ * two's complement of v (bit s-1 the sign); pos = Horner(bits) as in
+ * bfhe_bits_to_mod, neg = pos + (t - 2^s), and
+ *   out = isNeg * neg + (1 - isNeg) * pos,   isNeg = bits[s-1],
+ * an encryption of v mod t.  Needs 1 <= s and 2^s <= t, else BFHE_EINVAL.
+ * bits: uint64 [s][n][2][L][N] (bit 0 first); out: [n][2][L][N] (may alias
+ * bits).  2 multiplies (run as one batched multiply of 2n) and 2s + 1
+ * additions/subtractions per ciphertext; scratch from the context arena. */
+int bfhe_sint_to_mod(bfhe_ctx* ctx, const uint64_t* bits, uint32_t s, uint64_t* out, size_t n, void* stream);
+
+/* SecureMod -> SecureInt<s> (Sec. 3.2.4, Listing 9): pos = the conversion
+ * of bfhe_mod_to_bits applied to x over candidates [pos_lo, pos_hi];
+ * neg = the same conversion of (2^s - t) + x (SecureMod addition, mod t)
+ * over [neg_lo, neg_hi]; isNeg = pos[s-1]; bit k of the result is
+ *   isNeg * neg[k] + (1 - isNeg) * pos[k].
+ * This is the listing's arithmetic: where (2^s - t) + x wraps mod t the
+ * result is not the two's complement of x - t (Eq. 3 adds in bit-level
+ * arithmetic instead).  Needs 2^s >= t, s <= 63, both ranges inside
+ * [0, t), mode BFHE_PAPER or BFHE_SELECT, else BFHE_EINVAL.
+ * x: [n][2][L][N]; bits_out: [s][n][2][L][N] (may alias x).
+ * Multiplies: the two conversions' plus 2s per ciphertext (one batched
+ * multiply of 2sn). */
+int bfhe_mod_to_sint(bfhe_ctx* ctx, const uint64_t* x, uint32_t s, uint64_t pos_lo, uint64_t pos_hi,
+                     uint64_t neg_lo, uint64_t neg_hi, int mode, uint64_t* bits_out, size_t n, void* stream);
+
 /* Allocation-free variant of bfhe_mul_relin.  The paper has no counterpart:
  * this is for callers that cannot allocate device memory at call time --
  * code running under CUDA stream capture (where cudaMalloc and the device

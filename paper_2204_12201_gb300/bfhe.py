@@ -59,6 +59,8 @@ def load():
         "bfhe_gate_level": (I, [P, P, S, S, P, S, S, P]),
         "bfhe_bits_to_mod": (I, [P, P, U32, P, S, P]),
         "bfhe_mod_to_bits": (I, [P, P, U32, U64, U64, I, P, S, P]),
+        "bfhe_sint_to_mod": (I, [P, P, U32, P, S, P]),
+        "bfhe_mod_to_sint": (I, [P, P, U32, U64, U64, U64, U64, I, P, S, P]),
         "bfhe_pow": (I, [P, P, U64, P, S, P]),
         "bfhe_op_counts": (I, [P, P, I]),
         "bfhe_ntt": (I, [P, P, S, U32, I, P]),
@@ -227,6 +229,21 @@ class Context:
         n = self._n(x)
         out = self.empty_ct(n, s) if out is None else out
         _check(self.lib.bfhe_mod_to_bits(self.h, _ptr(x), s, c_lo, c_hi, mode, _ptr(out), n, self.stream))
+        return out
+
+    def sint_to_mod(self, bits, out=None):
+        """bits [s][n][2][L][N]: two's complement, sign bit last (Listing 6)."""
+        s, n = bits.shape[0], bits.shape[1]
+        out = self.empty_ct(n) if out is None else out
+        _check(self.lib.bfhe_sint_to_mod(self.h, _ptr(bits), s, _ptr(out), n, self.stream))
+        return out
+
+    def mod_to_sint(self, x, s, pos_range, neg_range, mode=PAPER, out=None):
+        """Listing 9; pos_range / neg_range = (lo, hi) candidates of x and of (2^s - t) + x."""
+        n = self._n(x)
+        out = self.empty_ct(n, s) if out is None else out
+        _check(self.lib.bfhe_mod_to_sint(self.h, _ptr(x), s, pos_range[0], pos_range[1], neg_range[0],
+                                         neg_range[1], mode, _ptr(out), n, self.stream))
         return out
 
     def pow(self, x, e, out=None):

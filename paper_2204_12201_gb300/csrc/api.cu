@@ -95,7 +95,8 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
     return BFHE_OK;
 }
 
-int scratch_for(bfhe_ctx* c, size_t fixed_words, size_t n_mul, u64** fixed, u64** mul, size_t* mul_words) {
+// multiply-scratch words granted to a call that keeps `fixed_words` and multiplies n_mul ciphertexts
+size_t mul_words_for(const bfhe_ctx* c, size_t fixed_words, size_t n_mul) {
     const size_t per = mul_words_per_ct(c);
     size_t budget_words = g_scratch_budget / sizeof(u64);
     size_t want_mul = n_mul * per;
@@ -103,7 +104,11 @@ int scratch_for(bfhe_ctx* c, size_t fixed_words, size_t n_mul, u64** fixed, u64*
         const size_t room = budget_words > fixed_words ? budget_words - fixed_words : 0;
         want_mul = std::max(per, (room / per) * per);
     }
-    if (n_mul == 0) want_mul = 0;
+    return n_mul == 0 ? 0 : want_mul;
+}
+
+int scratch_for(bfhe_ctx* c, size_t fixed_words, size_t n_mul, u64** fixed, u64** mul, size_t* mul_words) {
+    const size_t want_mul = mul_words_for(c, fixed_words, n_mul);
     void* p;
     RC(ctx_scratch(c, (fixed_words + want_mul) * sizeof(u64), &p));
     *fixed = (u64*)p;
@@ -481,26 +486,44 @@ extern "C" int bfhe_pow(bfhe_ctx* c, const uint64_t* x, uint64_t e, uint64_t* ou
     return pow_impl(c, x, e, out, n, fixed, mul, mw, st);
 }
 
-extern "C" int bfhe_mod_to_bits(bfhe_ctx* c, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
-                                uint64_t* bits_out, size_t n, void* stream) {
-    CHECK_CTX(c);
-    CHECK_KEYS(c);
-    if (n == 0) return BFHE_OK;
-    if (!x || !bits_out || s == 0 || s > 63 || c_hi < c_lo || c_hi >= c->t || (mode != BFHE_PAPER && mode != BFHE_SELECT))
-        return set_error(BFHE_EINVAL, "bad arguments");
-    cudaStream_t st = S(stream);
+namespace {
+
+// Scratch plan of one SecureMod -> SecureUint conversion: candidates per tile and the words it takes
+// after `reserve` words that the caller keeps at the front of the arena.
+struct M2BPlan {
+    size_t C, fixed_words, n_mul;
+};
+M2BPlan m2b_plan(const bfhe_ctx* c, uint32_t s, size_t total, int mode, size_t n, size_t reserve) {
     const size_t ctw = c->ct_words();
     const u64 e = c->t - 1;
-    const size_t total = c_hi - c_lo + 1;
     // candidates per tile: chain buffers (2 + popcount(e)) + PAPER's trivial bits, eq copies and products (3s)
     const size_t per_cand = n * ctw * (pow_buf_words(c, e, 1) / ctw + (mode == BFHE_PAPER ? 3 * s : 0) + 2);
     const size_t mul_per_cand = (mode == BFHE_PAPER ? s : 1) * n * mul_words_per_ct(c);
-    size_t C = (g_scratch_budget / sizeof(u64)) / (per_cand + mul_per_cand);
+    const size_t budget = g_scratch_budget / sizeof(u64);
+    const size_t room = budget > reserve ? budget - reserve : 0;
+    size_t C = room / (per_cand + mul_per_cand);
     if (C == 0) C = 1;
     if (C > total) C = total;
+    return {C, reserve + C * per_cand, C * (mode == BFHE_PAPER ? s : 1) * n};
+}
+
+bool m2b_args_ok(const bfhe_ctx* c, uint32_t s, u64 c_lo, u64 c_hi, int mode) {
+    return s != 0 && s <= 63 && c_hi >= c_lo && c_hi < c->t && (mode == BFHE_PAPER || mode == BFHE_SELECT);
+}
+
+// Sec. 3.2.3, Eq. 2, Listings 7-8; the first `reserve` words of the arena are left to the caller
+// (the arena must already hold them if they carry data: it is grown only when it is too small).
+int mod_to_bits_impl(bfhe_ctx* c, const u64* x, uint32_t s, u64 c_lo, u64 c_hi, int mode, u64* bits_out,
+                     size_t n, size_t reserve, cudaStream_t st) {
+    const size_t ctw = c->ct_words();
+    const u64 e = c->t - 1;
+    const size_t total = c_hi - c_lo + 1;
+    const M2BPlan pl = m2b_plan(c, s, total, mode, n, reserve);
+    const size_t C = pl.C;
     u64 *fixed, *mul;
     size_t mw;
-    RC(scratch_for(c, C * per_cand, C * (mode == BFHE_PAPER ? s : 1) * n, &fixed, &mul, &mw));
+    RC(scratch_for(c, pl.fixed_words, pl.n_mul, &fixed, &mul, &mw));
+    fixed += reserve;
     BFHE_CUDA(cudaMemsetAsync(bits_out, 0, (size_t)s * n * ctw * sizeof(u64), st));
     std::vector<size_t> terms(s, 0);
     for (size_t cb = 0; cb < total; cb += C) {
@@ -536,6 +559,101 @@ extern "C" int bfhe_mod_to_bits(bfhe_ctx* c, const uint64_t* x, uint32_t s, uint
     }
     for (uint32_t k = 0; k < s; ++k)
         if (terms[k] > 1) c->counts[0] += (uint64_t)(terms[k] - 1) * n;
+    return BFHE_OK;
+}
+
+}  // namespace
+
+extern "C" int bfhe_mod_to_bits(bfhe_ctx* c, const uint64_t* x, uint32_t s, uint64_t c_lo, uint64_t c_hi, int mode,
+                                uint64_t* bits_out, size_t n, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!x || !bits_out || !m2b_args_ok(c, s, c_lo, c_hi, mode)) return set_error(BFHE_EINVAL, "bad arguments");
+    return mod_to_bits_impl(c, x, s, c_lo, c_hi, mode, bits_out, n, 0, S(stream));
+}
+
+/* Sec. 3.2.2, Eq. 1, Listing 6.  One batched multiply of 2n: [isNeg; 1 - isNeg] x [neg; pos]. */
+extern "C" int bfhe_sint_to_mod(bfhe_ctx* c, const uint64_t* bits, uint32_t s, uint64_t* out, size_t n,
+                                void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!bits || !out || s == 0 || s > 63 || ((u64)1 << s) > c->t)
+        return set_error(BFHE_EINVAL, "bad arguments (need 1 <= s and 2^s <= t)");
+    cudaStream_t st = S(stream);
+    const size_t ctw = c->ct_words(), nw = n * ctw;
+    u64 *fixed, *mul;
+    size_t mw;
+    RC(scratch_for(c, 6 * nw, 2 * n, &fixed, &mul, &mw));
+    u64* A = fixed;       // [isNeg (n); 1 - isNeg (n)]
+    u64* B = A + 2 * nw;  // [neg (n); pos (n)]
+    u64* P = B + 2 * nw;  // the two products
+    const u64* is_neg = bits + (size_t)(s - 1) * nw;
+    RC(launch_horner(c, bits, s, B + nw, n, st));
+    RC(launch_lincomb(c, B, B + nw, nullptr, nullptr, nullptr, LinCoef{1, 1, 0, 0, 0},
+                      (c->t - ((u64)1 << s)) % c->t, n, st));
+    BFHE_CUDA(cudaMemcpyAsync(A, is_neg, nw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    RC(launch_lincomb(c, A + nw, is_neg, nullptr, nullptr, nullptr, LinCoef{1, -1, 0, 0, 0}, 1, n, st));
+    RC(mul_relin_impl(c, A, B, P, 2 * n, mul, mw, st));
+    RC(launch_lincomb(c, out, P, P + nw, nullptr, nullptr, LinCoef{0, 1, 1, 0, 0}, 0, n, st));
+    c->counts[0] += (uint64_t)(2 * (s - 1) + 2) * n;
+    c->counts[1] += n;
+    c->counts[2] += 2 * n;
+    return BFHE_OK;
+}
+
+/* Sec. 3.2.4, Listing 9: two SecureMod -> SecureUint conversions (of x and of (2^s - t) + x) and a
+ * multiplexer on the sign bit of the first, batched as one multiply of 2sn. */
+extern "C" int bfhe_mod_to_sint(bfhe_ctx* c, const uint64_t* x, uint32_t s, uint64_t pos_lo, uint64_t pos_hi,
+                                uint64_t neg_lo, uint64_t neg_hi, int mode, uint64_t* bits_out, size_t n,
+                                void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!x || !bits_out || !m2b_args_ok(c, s, pos_lo, pos_hi, mode) || !m2b_args_ok(c, s, neg_lo, neg_hi, mode))
+        return set_error(BFHE_EINVAL, "bad arguments");
+    if (((u64)1 << s) < c->t) return set_error(BFHE_EINVAL, "bad arguments (need 2^s >= t)");
+    cudaStream_t st = S(stream);
+    const size_t ctw = c->ct_words(), nw = n * ctw, sn = (size_t)s * n;
+    // kept across the stages: BITS = [neg (s n); pos (s n)] and the shifted input (n)
+    const size_t reserve = 2 * sn * ctw + nw;
+    const size_t mux_fixed = reserve + 4 * sn * ctw;
+    // size the arena once for the largest stage, so that no stage regrows it under kept data
+    const M2BPlan p1 = m2b_plan(c, s, pos_hi - pos_lo + 1, mode, n, reserve);
+    const M2BPlan p2 = m2b_plan(c, s, neg_hi - neg_lo + 1, mode, n, reserve);
+    size_t need = mux_fixed + mul_words_for(c, mux_fixed, 2 * sn);
+    need = std::max(need, p1.fixed_words + mul_words_for(c, p1.fixed_words, p1.n_mul));
+    need = std::max(need, p2.fixed_words + mul_words_for(c, p2.fixed_words, p2.n_mul));
+    void* base;
+    RC(ctx_scratch(c, need * sizeof(u64), &base));
+    u64* NEG = (u64*)base;
+    u64* POS = NEG + sn * ctw;
+    u64* XS = POS + sn * ctw;
+    RC(mod_to_bits_impl(c, x, s, pos_lo, pos_hi, mode, POS, n, reserve, st));
+    RC(launch_lincomb(c, XS, x, nullptr, nullptr, nullptr, LinCoef{1, 1, 0, 0, 0}, (((u64)1 << s) - c->t) % c->t,
+                      n, st));
+    c->counts[0] += n;
+    RC(mod_to_bits_impl(c, XS, s, neg_lo, neg_hi, mode, NEG, n, reserve, st));
+    u64 *fixed, *mul;
+    size_t mw;
+    RC(scratch_for(c, mux_fixed, 2 * sn, &fixed, &mul, &mw));
+    if (fixed != (u64*)base) return set_error(BFHE_ESTATE, "scratch moved between stages");
+    u64* A = fixed + reserve;   // [isNeg x s; (1 - isNeg) x s] against [neg; pos]
+    u64* P = A + 2 * sn * ctw;  // products
+    const u64* is_neg = POS + (size_t)(s - 1) * nw;
+    RC(launch_lincomb(c, A + sn * ctw, is_neg, nullptr, nullptr, nullptr, LinCoef{1, -1, 0, 0, 0}, 1, n, st));
+    c->counts[1] += n;
+    for (uint32_t k = 0; k < s; ++k) {
+        BFHE_CUDA(cudaMemcpyAsync(A + (size_t)k * nw, is_neg, nw * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+        if (k)
+            BFHE_CUDA(cudaMemcpyAsync(A + (s + k) * nw, A + sn * ctw, nw * sizeof(u64), cudaMemcpyDeviceToDevice,
+                                      st));
+    }
+    RC(mul_relin_impl(c, A, NEG, P, 2 * sn, mul, mw, st));
+    c->counts[2] += 2 * sn;
+    RC(launch_lincomb(c, bits_out, P, P + sn * ctw, nullptr, nullptr, LinCoef{0, 1, 1, 0, 0}, 0, sn, st));
+    c->counts[0] += sn;
     return BFHE_OK;
 }
 

@@ -270,3 +270,47 @@ def test_mul_relin_at_benchmark_parameters():
     sq = P.ctx.mul_relin(got, got)
     p = (y[0] * y[1]) % prm.t
     assert np.array_equal(P.ctx.decrypt(sq).cpu().numpy()[0], (p * p) % prm.t)
+
+
+# ------------------------------------------------------------ signed conversions (Listings 6 and 9)
+@pytest.mark.parametrize("name,cfg,s", [("LOW_T", LOW_T, 1), ("LOW_T", LOW_T, 13), ("C1", C1, 8), ("C1", C1, 16)])
+def test_sint_to_mod(name, cfg, s):
+    """Two's complement bit planes of signed slots -> SecureMod, against the oracle bit for bit;
+    the result decrypts to v mod t (depth 1)."""
+    P = pair(name, cfg)
+    prm = P.prm
+    v = inputs.slots(20 + s, 1, prm.N, lo=-(1 << (s - 1)), hi=1 << (s - 1))[0]
+    v[:2] = [-(1 << (s - 1)), (1 << (s - 1)) - 1]          # both ends of the range
+    planes = inputs.bit_planes(v % (1 << s), s)
+    bits = [P.enc(planes[k], 121, k) for k in range(s)]
+    dev = cts_to_device(prm, bits)[:, None]                  # [s][1][2][L][N]
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.sint_to_mod(bits)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.sint_to_mod(dev)
+    assert_ct_equal(prm, got, [want], "sint_to_mod s=%d" % s)
+    assert P.ctx.op_counts()[:3] == ev.counts()
+    assert np.array_equal(P.ctx.decrypt(got).cpu().numpy()[0], v % prm.t)
+
+
+@pytest.mark.parametrize("sign,mode", [(+1, bridge.PAPER), (-1, bridge.SELECT)])
+def test_mod_to_sint(sign, mode):
+    """Listing 9 at t = 12289, s = 14 (2^s >= t): slots all non-negative (x in [0, 2)) or all
+    negative (x in [t-4, t)); candidate ranges are the values x and (2^s - t) + x take."""
+    P = pair("LOW_T", LOW_T)
+    prm = P.prm
+    t, s = prm.t, 14
+    lo, hi = (0, 1) if sign > 0 else (t - 4, t - 1)
+    xs = inputs.slots(30 + sign, 1, prm.N, lo=lo, hi=hi + 1)[0]
+    x = P.enc(xs, 131, 0)
+    shift = ((1 << s) - t) % t
+    pos_r = (lo, hi)
+    neg_r = ((lo + shift) % t, (hi + shift) % t)
+    assert neg_r[0] <= neg_r[1]
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.mod_to_sint(x, s, range(pos_r[0], pos_r[1] + 1), range(neg_r[0], neg_r[1] + 1), mode)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.mod_to_sint(cts_to_device(prm, [x]), s, pos_r, neg_r, mode)
+    for k in range(s):
+        assert_ct_equal(prm, got[k], [want[k]], "mod_to_sint bit %d" % k)
+    assert P.ctx.op_counts()[:3] == ev.counts()
