@@ -17,10 +17,24 @@ little-endian lists of ciphertexts (bit 0 first).
 * shift-add multiplier: partial products a AND b_j, accumulated row by row
   with the ripple-carry adder (2n-bit product);
 * argmax of three: i1 = [s0' < s2], i0 = [s0 < s1] AND NOT i1 where
-  s0' = MUX([s0 < s1], s1, s0); ties keep the lower index.
+  s0' = MUX([s0 < s1], s1, s0); ties keep the lower index;
+* equality: e_k = XNOR(x_k, y_k), then a balanced AND tree (low half
+  [0, n//2) times high half), 2n - 1 multiplies;
+* increment by the public 1: bit 0 is NOT x_0 with carry x_0 (XOR and AND
+  with a public 1 are exact rewrites, no multiply), then half adders; the
+  carry out of the top bit is dropped (n-bit wraparound), n - 1 multiplies.
+
+Fibonacci (Sec. 2.2 and 3.1, Listings 3 and 4): the data-oblivious loop
+r += (i++ == in) * a; swap(a, b); a += b, max_iter times.  The initial
+values i = 0, a = 0, b = 1, r = 0 are encrypted constants in E3; here they
+are input ciphertexts.  The bit-level program keeps i, a, b, r as n-bit
+SecureUint (r += e * a is an n-bit AND of e with a then an n-bit ripple add,
+sums wrap mod 2^n); the bridged one keeps a, b, r as SecureMod, so the
+SecureBool e is cast by Horner's scheme with one bit (the identity) and
+r += e * a is one ciphertext multiply and one addition.
 """
 
-from .bridge import AND, MUX, NOT
+from .bridge import AND, MUX, NOT, XNOR
 
 
 def half_adder_shared(ev, x, y):
@@ -94,3 +108,46 @@ def argmax3(ev, s0, s1, s2):
     i1 = less_than(ev, best, s2)
     i0 = ev.gate(AND, lt01, ev.gate(NOT, i1))
     return [i0, i1]
+
+
+def equal(ev, x, y):
+    """Encryption of [x == y] for little-endian bit vectors of equal length."""
+    e = [ev.gate(XNOR, xi, yi) for xi, yi in zip(x, y)]
+
+    def tree(lo, hi):
+        if hi - lo == 1:
+            return e[lo]
+        mid = lo + (hi - lo) // 2
+        return ev.mul(tree(lo, mid), tree(mid, hi))
+    return tree(0, len(e))
+
+
+def increment(ev, x):
+    """x + 1 mod 2^n."""
+    out = [ev.gate(NOT, x[0])]
+    c = x[0]
+    for k in range(1, len(x)):
+        s, c = half_adder_shared(ev, x[k], c)
+        out.append(s)
+    return out
+
+
+def fibonacci_bits(ev, inp, i, a, b, r, max_iter):
+    """Listing 3: every variable an n-bit SecureUint (lists of bit ciphertexts)."""
+    n = len(inp)
+    for _ in range(max_iter):
+        e = equal(ev, i, inp)
+        i = increment(ev, i)
+        r = ripple_add(ev, [ev.gate(AND, e, ak) for ak in a], r)[:n]
+        a, b = ripple_add(ev, b, a)[:n], a
+    return r
+
+
+def fibonacci_bridged(ev, inp, i, a, b, r, max_iter):
+    """Listing 4: in and i n-bit SecureUint; a, b, r SecureMod ciphertexts."""
+    for _ in range(max_iter):
+        e = equal(ev, i, inp)
+        i = increment(ev, i)
+        r = ev.add(r, ev.mul(ev.bits_to_mod([e]), a))
+        a, b = ev.add(b, a), a
+    return r

@@ -23,7 +23,17 @@ Netlists (the same structure the tests' oracle circuits follow):
   where a parent uses it; low block = bits [0, n/2);
 * shift-add multiplier: partial products a_i b_j, rows added by ripple
   adders (the first row is one bit shorter and zero-extended);
-* argmax of three: i1 = [max(s0, s1) < s2], i0 = [s0 < s1] AND NOT i1.
+* argmax of three: i1 = [max(s0, s1) < s2], i0 = [s0 < s1] AND NOT i1;
+* equality: XNOR per bit (1 - (x + y - 2xy)), then a balanced product tree
+  (low half [0, n/2) times high half);
+* increment by the public 1: bit 0 = NOT x_0, carry x_0, then half adders,
+  top carry dropped.
+
+Fibonacci (Listings 3 and 4): max_iter rounds of r += (i++ == in) * a;
+swap(a, b); a += b, with the initial values as input wires.  Bit-level: a,
+b, r are n-bit words (AND of e with a, ripple adds truncated to n bits);
+bridged: a, b, r are single SecureMod wires, the SecureBool e is cast by
+one-bit Horner (the wire itself), r += e * a is one MUL and one LIN.
 """
 
 import torch
@@ -124,6 +134,44 @@ class Netlist:
         for j in range(1, n):
             acc = acc[:j] + self.ripple_add(acc[j:], rows[j])
         return acc
+
+    def XNOR(self, x, y):
+        p = self.mul(x, y)
+        return self.lin([(x, -1), (y, -1), (p, 2)], 1)
+
+    def equal(self, x, y):
+        e = [self.XNOR(xi, yi) for xi, yi in zip(x, y)]
+
+        def tree(lo, hi):
+            if hi - lo == 1:
+                return e[lo]
+            mid = lo + (hi - lo) // 2
+            return self.mul(tree(lo, mid), tree(mid, hi))
+        return tree(0, len(e))
+
+    def increment(self, x):
+        out, c = [self.NOT(x[0])], x[0]
+        for k in range(1, len(x)):
+            sk, c = self.half_adder(x[k], c)
+            out.append(sk)
+        return out
+
+    def fibonacci_bits(self, inp, i, a, b, r, max_iter):
+        n = len(inp)
+        for _ in range(max_iter):
+            e = self.equal(i, inp)
+            i = self.increment(i)
+            r = self.ripple_add([self.AND(e, ak) for ak in a], r)[:n]
+            a, b = self.ripple_add(b, a)[:n], a
+        return r
+
+    def fibonacci_bridged(self, inp, i, a, b, r, max_iter):
+        for _ in range(max_iter):
+            e = self.equal(i, inp)
+            i = self.increment(i)
+            r = self.lin([(r, 1), (self.mul(e, a), 1)])
+            a, b = self.lin([(b, 1), (a, 1)]), a
+        return r
 
     def argmax3(self, s0, s1, s2):
         lt01 = self.less_than(s0, s1)

@@ -66,3 +66,57 @@ class GenotypeJob:
         if keep:
             self.last = {"enc": g, "scores": scores, "bits": bits, "idx": idx}
         return ctx.decrypt(idx)                                                # [2][N] index bits
+
+
+class FibonacciJob:
+    """The data-oblivious Fibonacci of Listings 3 (bit-level) and 4 (bridged) over every slot.
+
+    Slot j of batch entry b computes fibonacci(in[b, j]) for its own input.
+    The initial values i = 0, a = 0, b = 1, r = 0 are fresh encryptions (E3
+    encrypts the constants `_0_E`, `_1_M`), made with the input bits in one
+    batched encrypt call; input wire w of batch entry b is ciphertext
+    w * n + b of that call.
+    """
+
+    def __init__(self, ctx, kind, width=8, max_iter=10, n=1):
+        assert kind in ("bits", "bridged")
+        self.ctx, self.kind, self.width, self.max_iter, self.n = ctx, kind, width, max_iter, n
+        net = circuits.Netlist()
+        inp, i0 = net.inputs(width), net.inputs(width)
+        if kind == "bits":
+            a0, b0, r0 = (net.inputs(width) for _ in range(3))
+            self.out_wires = net.fibonacci_bits(inp, i0, a0, b0, r0, max_iter)
+            self.consts = [0] * (2 * width) + [1] + [0] * (2 * width - 1)      # i, a, b, r
+        else:
+            a0, b0, r0 = net.inputs(3)
+            self.out_wires = [net.fibonacci_bridged(inp, i0, a0, b0, r0, max_iter)]
+            self.consts = [0] * width + [0, 1, 0]
+        self.net = net
+        self.circ = circuits.Compiled(ctx, net, n)
+
+    def input_slots(self, vals):
+        """vals: device int64 [n][N] inputs -> slot values of every input wire [n_inputs][n][N]."""
+        import torch
+        planes = torch.stack([(vals >> k) & 1 for k in range(self.width)])
+        c = torch.tensor(self.consts, dtype=torch.int64, device=vals.device).view(-1, 1, 1)
+        return torch.cat([planes, c.expand(-1, vals.shape[0], vals.shape[1])])
+
+    def set_inputs(self, vals, seed):
+        slots = self.input_slots(vals)
+        cts = self.ctx.encrypt(slots.reshape(-1, self.ctx.N), seed)
+        self.circ.set_inputs(cts.view(slots.shape[0], self.n, 2, self.ctx.L, self.ctx.N))
+
+    def run(self):
+        self.circ.run()
+
+    def result(self):
+        """[len(out)][n][2][L][N]: the bits of r (bit-level) or the single SecureMod r."""
+        return self.circ.out(self.out_wires)
+
+    def decrypt(self):
+        """Decrypted r per slot: [n][N] (bits recombined for the bit-level program)."""
+        out = self.result()
+        d = [self.ctx.decrypt(out[k].contiguous()) for k in range(out.shape[0])]
+        if self.kind == "bridged":
+            return d[0]
+        return sum(dk << k for k, dk in enumerate(d))

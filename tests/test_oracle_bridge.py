@@ -307,3 +307,81 @@ def test_mod_to_sint_against_eq3(t, s):
             assert v % t == x                     # the signed value is congruent to x
         else:
             assert g == ((1 << s) - t + x) % t, x
+
+
+# ------------------------------------------------------------ Fibonacci (Listings 1-4)
+def _fib_plain(n_in):
+    """Listing 1: the plain loop, run until i reaches the input."""
+    i, a, b = 0, 0, 1
+    while i != n_in:
+        i += 1
+        a, b = b, a
+        a += b
+    return a
+
+
+def _fib_oblivious(n_in, max_iter, width):
+    """Listing 2 with the counter i kept in `width` bits (it wraps like the encrypted one)."""
+    i, a, b, r = 0, 0, 1, 0
+    for _ in range(max_iter):
+        r += (i == n_in) * a
+        i = (i + 1) % (1 << width)
+        a, b = b, a
+        a += b
+    return r
+
+
+def test_fibonacci_listings_agree():
+    assert [_fib_plain(k) for k in range(12)] == [0, 1, 1, 2, 3, 5, 8, 13, 21, 34, 55, 89]
+    for k in range(10):
+        assert _fib_oblivious(k, 10, 8) == _fib_plain(k)
+    assert _fib_oblivious(12, 10, 8) == 0            # the accumulator never reaches the input
+
+
+@pytest.mark.parametrize("width,max_iter", [(4, 10), (4, 20), (8, 10), (8, 16)])
+def test_fibonacci_bit_level_and_bridged_plain(width, max_iter):
+    """Every input value in its own slot: Listing 3 equals Listing 2 mod 2^width, Listing 4 mod t;
+    multiply counts per iteration 8n - 4 (bit-level) and 3n - 1 (bridged)."""
+    t = 65537
+    vals = list(range(1 << width))
+    n = len(vals)
+    inp = _bits(vals, width)
+    zero, one = [0] * n, [1] * n
+    want = [_fib_oblivious(v, max_iter, width) for v in vals]
+
+    ev = PlainEvaluator(t, n)
+    r = circuits.fibonacci_bits(ev, inp, [zero] * width, [zero] * width, [one] + [zero] * (width - 1),
+                                [zero] * width, max_iter)
+    assert _val(r) == [w % (1 << width) for w in want]
+    assert ev.n_mul == max_iter * (8 * width - 4)
+
+    ev = PlainEvaluator(t, n)
+    r = circuits.fibonacci_bridged(ev, inp, [zero] * width, zero, one, zero, max_iter)
+    assert r == [w % t for w in want]
+    assert ev.n_mul == max_iter * (3 * width - 1)
+
+
+def test_equal_and_increment_plain():
+    rng = random.Random(12)
+    x = [rng.randrange(256) for _ in range(300)] + [0, 255, 17]
+    y = [rng.randrange(256) if k % 3 else x[k] for k in range(300)] + [0, 255, 18]
+    ev = PlainEvaluator(65537, len(x))
+    assert circuits.equal(ev, _bits(x, 8), _bits(y, 8)) == [int(a == b) for a, b in zip(x, y)]
+    assert ev.n_mul == 15
+    ev = PlainEvaluator(65537, len(x))
+    assert _val(circuits.increment(ev, _bits(x, 8))) == [(a + 1) % 256 for a in x]
+    assert ev.n_mul == 7
+
+
+def test_fibonacci_encrypted_small(tiny):
+    """Both programs on encrypted 2-bit inputs (t = 17), one slot per input value."""
+    prm, keys = tiny
+    width, max_iter = 2, 3
+    vals = [0, 1, 2, 3, 0, 1, 2, 3]
+    enc = lambda v, k: bfv.encrypt(prm, keys, v, 141, k)
+    z, o = [0] * prm.N, [1] * prm.N
+    inp = [enc(p, k) for k, p in enumerate(_bits(vals, width))]
+    zeros = [enc(z, 10 + k) for k in range(width)]
+    ev = bridge.Evaluator(prm, keys)
+    r = circuits.fibonacci_bridged(ev, inp, zeros, enc(z, 20), enc(o, 21), enc(z, 22), max_iter)
+    assert bfv.decrypt(prm, keys, r) == [_fib_oblivious(v, max_iter, width) % prm.t for v in vals]
