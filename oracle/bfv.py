@@ -6,7 +6,9 @@ ciphertext bits is stated here so that the CUDA library can reproduce it:
 
 * ring R = Z[X]/(X^N + 1); ciphertexts are pairs of polynomials with
   coefficients in [0, Q); keys and randomness come from `philox`;
-* slots (FHE batching, Sec. 2.3): slot j holds m(zeta^(2j+1)) mod t;
+* slots (FHE batching, Sec. 2.3): slot j holds m(zeta^(2j+1)) mod t; with
+  t = 2 there are no slots and encrypt_poly / decrypt_poly carry the
+  plaintext polynomial's coefficients directly;
 * pk = ([-(a s + e)]_Q, a); relinearisation key for digit j = 0..L-1:
   rlk_j = ([-(a_j s + e_j) + P g_j s^2]_{PQ}, a_j) with the RNS gadget
   g_j = (Q/q_j) * [(Q/q_j)^-1]_{q_j};
@@ -111,8 +113,14 @@ def keygen(prm, seed):
 # ---------------------------------------------------------------- encrypt / decrypt
 def encrypt(prm, keys, slots, seed, idx=0):
     """Public-key encryption of one slot vector; idx selects the randomness stream."""
+    if not prm.batching:
+        raise ValueError("no batching at t = %d" % prm.t)
+    return encrypt_poly(prm, keys, encode_slots(prm, slots), seed, idx)
+
+
+def encrypt_poly(prm, keys, m, seed, idx=0):
+    """Public-key encryption of the plaintext polynomial m (coefficients in [0, t))."""
     N, Q = prm.N, prm.Q
-    m = encode_slots(prm, slots)
     u = px.ternary_poly(seed, px.ENC_U, idx, N)
     e1 = px.cbd_poly(seed, px.ENC_E1, idx, N)
     e2 = px.cbd_poly(seed, px.ENC_E2, idx, N)
@@ -144,6 +152,8 @@ def decrypt_poly(prm, keys, ct):
 
 
 def decrypt(prm, keys, ct):
+    if not prm.batching:
+        raise ValueError("no batching at t = %d" % prm.t)
     return decode_poly(prm, decrypt_poly(prm, keys, ct))
 
 

@@ -5,7 +5,8 @@ Test infrastructure only.  Follows the paper directly:
 * gate equations over encrypted bits (Sec. 3.1): AND = xy, NAND = 1 - xy,
   OR = x + y - xy, NOR = 1 - OR, XOR = x + y - 2xy, XNOR = 1 - XOR,
   NOT = 1 - x, MUX(x, y, z) = x(y - z) + z; one ciphertext multiply per gate
-  except NOT;
+  except NOT; with t = 2 the XOR equation reduces to x + y (mod 2) and XOR and
+  XNOR = 1 - (x + y) take no multiply (Sec. 3.1, Sec. 4.3);
 * SecureUint -> SecureMod (Sec. 3.2.1, Listing 5): Horner, r = v[s-1];
   r += r + v[i] for i = s-2 .. 0; 2(s-1) additions, no multiplies;
 * pow (Listing 7): square-and-multiply recursion, floor(log2 e) + w(e) - 1
@@ -87,6 +88,9 @@ class Evaluator:
             return self.const_sub(1, x)
         if g == MUX:
             return self.add(self.mul(x, self.sub(y, z)), z)
+        if self.prm.t == 2 and g in (XOR, XNOR):
+            r = self.add(x, y)
+            return r if g == XOR else self.const_sub(1, r)
         xy = self.mul(x, y)
         if g == AND:
             return xy

@@ -9,7 +9,8 @@ little-endian lists of ciphertexts (bit 0 first).
   s_i = u_i XOR c_i (= u_i + c_i - 2 q_i), c_{i+1} = p_i + q_i (the two terms
   are never both 1); c_0 = 0 is public, so bit 0 is a half adder; the carry
   out is kept (n + 1 output bits); XOR here is x + y - 2xy with the product
-  shared with the carry logic, so an n-bit adder costs 2n - 1 multiplies;
+  shared with the carry logic, so an n-bit adder costs 2n - 1 multiplies
+  (with t = 2 the sums are x + y and the products serve the carries only);
 * less-than comparator, balanced: a leaf is (lt, eq) = ((1 - a_i) b_i,
   1 - (a_i XOR b_i)); two blocks merge high over low as
   lt = lt_H + eq_H lt_L, eq = eq_H eq_L (eq only where a parent uses it);
@@ -38,8 +39,10 @@ from .bridge import AND, MUX, NOT, XNOR
 
 
 def half_adder_shared(ev, x, y):
-    """(x XOR y, x AND y) with one shared multiply."""
+    """(x XOR y, x AND y) with one shared multiply (with t = 2 the sum is x + y alone)."""
     p = ev.mul(x, y)
+    if ev.prm.t == 2:
+        return ev.add(x, y), p
     u = ev.sub(ev.add(x, y), ev.add(p, p))
     return u, p
 
@@ -73,10 +76,7 @@ def less_than(ev, a, b):
     def block(lo, hi, need_eq):
         if hi - lo == 1:
             lt = ev.mul(ev.const_sub(1, a[lo]), b[lo])
-            eq = None
-            if need_eq:
-                u, _ = half_adder_shared(ev, a[lo], b[lo])
-                eq = ev.const_sub(1, u)
+            eq = ev.gate(XNOR, a[lo], b[lo]) if need_eq else None
             return lt, eq
         mid = lo + (hi - lo) // 2
         lt_l, eq_l = block(lo, mid, need_eq)

@@ -12,7 +12,10 @@ pick the rest (Sec. 4.1).  This build fixes the remaining choices as follows:
   (|d| <= N Q^2 / 2) and the rounded quotient round(t d / Q) representable
   in the centred range of the moduli QB and B respectively;
 * Delta = floor(Q / t); the slot root is zeta = g^((t-1)/2N) mod t with g the
-  least primitive root of t.
+  least primitive root of t;
+* t = 2 (Sec. 4.1 and 4.3 run the bit-level benchmarks with t = 2 as well):
+  no batching (2 is not 1 mod 2N), so plaintexts are polynomials with
+  coefficients mod 2 and there is no slot root.
 """
 
 from dataclasses import dataclass, field
@@ -51,13 +54,15 @@ class Params:
     K: int = 0
     delta: int = 0
     zeta: int = 0
+    batching: bool = True
 
     def __post_init__(self):
         N, t = self.N, self.t
         if N & (N - 1) or N < 2:
             raise ValueError("N must be a power of two")
-        if not is_prime(t) or (t - 1) % (2 * N):
-            raise ValueError("batching needs a prime t = 1 mod 2N")
+        self.batching = t != 2
+        if self.batching and (not is_prime(t) or (t - 1) % (2 * N)):
+            raise ValueError("batching needs a prime t = 1 mod 2N (or t = 2 without batching)")
         head = scan_primes(N, self.L + self.alpha, self.prime_bits, exclude=(t,))
         self.q = head[: self.L]
         self.p = head[self.L:]
@@ -75,8 +80,9 @@ class Params:
         self.B = B
         self.K = K
         self.delta = self.Q // t
-        g = least_primitive_root(t)
-        self.zeta = pow(g, (t - 1) // (2 * N), t)
+        if self.batching:
+            g = least_primitive_root(t)
+            self.zeta = pow(g, (t - 1) // (2 * N), t)
 
     @property
     def PQ(self):

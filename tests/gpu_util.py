@@ -33,3 +33,10 @@ def assert_ct_equal(prm, got, want_cts, what=""):
         if not np.array_equal(g[i], wr):
             bad = np.argwhere(g[i] != wr)
             raise AssertionError("%s: ciphertext %d differs at %d words, first %s" % (what, i, len(bad), bad[:4].tolist()))
+
+
+def rns_to_ct(prm, arr):
+    """int64 [2][L][N] residues from the device -> oracle ciphertext (two lists over Z_Q)."""
+    from oracle import bfv
+    a = np.asarray(arr)
+    return tuple(bfv.from_rns([[int(v) for v in a[c, i]] for i in range(prm.L)], prm.q) for c in range(a.shape[0]))

@@ -26,6 +26,7 @@ WIDE = dict(N=32768, L=2, alpha=2)         # N = 32768: the two-pass NTT path
 LOW_T = dict(N=1024, L=2, alpha=1, t=12289)  # t - 1 = 3 * 2^12: pow with an odd step
 MID = dict(N=16384, L=2, alpha=1)          # N = 16384: split-half forward NTT, whole-limb inverse
 C4 = dict(N=16384, L=8, alpha=1)           # the benchmark's parameters
+L16 = dict(N=1024, L=16, alpha=2)          # the largest limb count, two special primes (the bridge workload's)
 
 
 class Pair:
@@ -132,7 +133,8 @@ def test_linear_ops():
 
 
 @pytest.mark.parametrize("name,cfg,n", [("C1", C1, 3), ("SMALL", SMALL, 2), ("ALPHA2", ALPHA2, 2),
-                                        ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2), ("MID", MID, 1)])
+                                        ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2), ("MID", MID, 1),
+                                        ("L16", L16, 2)])
 def test_mul_relin(name, cfg, n):
     P = pair(name, cfg)
     prm = P.prm
@@ -241,7 +243,7 @@ def test_gate_level_matches_gates():
         assert_ct_equal(prm, wires[3 + i], [want], "level gate %s" % bridge.GATE_NAMES[g])
 
 
-@pytest.mark.parametrize("name,cfg", [("C1", C1), ("ALPHA2", ALPHA2)])
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("ALPHA2", ALPHA2), ("L16", L16)])
 def test_square_path(name, cfg):
     """mul_relin(x, x) through the squaring path equals the oracle's x * x."""
     P = pair(name, cfg)
