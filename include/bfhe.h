@@ -58,7 +58,9 @@ typedef struct {
     uint32_t L;          /* data primes, 1 .. 16                               */
     uint32_t alpha;      /* special primes, 1 or 2                             */
     uint32_t prime_bits; /* bit size of every modulus, 30 .. 60 (default 50)   */
-    uint64_t t;          /* plaintext modulus: a prime = 1 (mod 2N), < 2^32    */
+    uint64_t t;          /* plaintext modulus: a prime = 1 (mod 2N), < 2^32,   */
+                         /* or 2 (no batching: coefficient encoding only,      */
+                         /* Sec. 4.1 and 4.3 run bit-level arithmetic at t = 2) */
 } bfhe_params;
 
 /* Create a context on CUDA device `device`.  Builds the moduli, NTT twiddles
@@ -93,13 +95,25 @@ int bfhe_export_keys(bfhe_ctx* ctx, int64_t* sk, uint64_t* pk, uint64_t* rlk, vo
 /* Encrypt n slot vectors (slots uint64 [n][N], each < t) into ct_out
  * [n][2][L][N]: (Delta m + pk0 u + e1, pk1 u + e2) mod Q with m the batch
  * encoding (slot j = m(zeta^(2j+1)) mod t, Sec. 2.3) and u, e1, e2 drawn
- * from Philox4x64-10 with key (seed, purpose) and poly index = batch index. */
+ * from Philox4x64-10 with key (seed, purpose) and poly index = batch index.
+ * BFHE_EINVAL at t = 2 (no slots). */
 int bfhe_encrypt(bfhe_ctx* ctx, const uint64_t* slots, size_t n, uint64_t seed,
                  uint64_t* ct_out, void* stream);
 
 /* Decrypt n ciphertexts into slots uint64 [n][N]: m = [round(t [c0 + c1 s]_Q
- * / Q)]_t computed exactly, then decoded. */
+ * / Q)]_t computed exactly, then decoded.  BFHE_EINVAL at t = 2. */
 int bfhe_decrypt(bfhe_ctx* ctx, const uint64_t* ct, size_t n, uint64_t* slots_out, void* stream);
+
+/* Coefficient encoding (any t; the only encoding at t = 2): encrypt n
+ * plaintext polynomials coeffs uint64 [n][N] (coefficient k of polynomial
+ * i at [i][k], each < t; larger values are a precondition violation that
+ * encrypts the unreduced value, not an error) with the same randomness as
+ * bfhe_encrypt; a product of two such ciphertexts encrypts the negacyclic
+ * product of the polynomials mod t.  Decrypt returns the coefficients
+ * [round(t [c0 + c1 s]_Q / Q)]_t into coeffs_out [n][N]. */
+int bfhe_encrypt_poly(bfhe_ctx* ctx, const uint64_t* coeffs, size_t n, uint64_t seed, uint64_t* ct_out,
+                      void* stream);
+int bfhe_decrypt_poly(bfhe_ctx* ctx, const uint64_t* ct, size_t n, uint64_t* coeffs_out, void* stream);
 
 /* Linear operations (Sec. 3.1 uses them in every gate; Listing 5 is only
  * additions).  out may alias a or b.  A public constant c (< t) enters as
@@ -128,14 +142,18 @@ int bfhe_mul_relin(bfhe_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t
  * NAND = 1 - xy, OR = x + y - xy, NOR = 1 - OR, XOR = x + y - 2xy,
  * XNOR = 1 - XOR, NOT = 1 - x, MUX(x, y, z) = x (y - z) + z.
  * y is ignored for NOT; z is used by MUX only.  One multiply per gate
- * (none for NOT).  out must not alias the inputs. */
+ * (none for NOT).  At t = 2 XOR = x + y and XNOR = 1 - (x + y), without a
+ * multiply (Sec. 3.1).  out must not alias the inputs of a multiplying
+ * gate. */
 enum { BFHE_AND = 0, BFHE_OR = 1, BFHE_XOR = 2, BFHE_NAND = 3, BFHE_NOR = 4, BFHE_XNOR = 5,
        BFHE_NOT = 6, BFHE_MUX = 7 };
 int bfhe_bit_gate(bfhe_ctx* ctx, int gate, const uint64_t* x, const uint64_t* y, const uint64_t* z,
                   uint64_t* out, size_t n, void* stream);
 
 /* A levelised gate list over one wire array: all multiplying entries of one
- * circuit depth level share one batched multiply.  wires: uint64
+ * circuit depth level share one batched multiply.  Gate entries run the
+ * Sec. 3.1 equations as written at every t (a netlist for t = 2 writes its
+ * XORs as linear entries).  wires: uint64
  * [n_wires][n][2][L][N] (n slot-packed ciphertexts per wire); table: DEVICE
  * int32 [n_gates][5] = (op, x, y, z, out) wire indices, the n_mul entries
  * with a multiply first.  op is a gate above (BFHE_AND .. BFHE_MUX, with the

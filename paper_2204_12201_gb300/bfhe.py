@@ -60,6 +60,8 @@ def load():
         "bfhe_bits_to_mod": (I, [P, P, U32, P, S, P]),
         "bfhe_mod_to_bits": (I, [P, P, U32, U64, U64, I, P, S, P]),
         "bfhe_sint_to_mod": (I, [P, P, U32, P, S, P]),
+        "bfhe_encrypt_poly": (I, [P, P, S, U64, P, P]),
+        "bfhe_decrypt_poly": (I, [P, P, S, P, P]),
         "bfhe_mod_to_sint": (I, [P, P, U32, U64, U64, U64, U64, I, P, S, P]),
         "bfhe_pow": (I, [P, P, U64, P, S, P]),
         "bfhe_op_counts": (I, [P, P, I]),
@@ -157,6 +159,25 @@ class Context:
         n = slots.numel() // self.N
         out = self.empty_ct(n) if out is None else out
         _check(self.lib.bfhe_encrypt(self.h, _ptr(slots), n, seed, _ptr(out), self.stream))
+        return out
+
+    @property
+    def batching(self):
+        """False at t = 2: coefficient encoding only (encrypt_poly / decrypt_poly)."""
+        return self.t != 2
+
+    def encrypt_poly(self, coeffs, seed, out=None):
+        """coeffs [n][N] plaintext polynomials (coefficients < t)."""
+        coeffs = coeffs.contiguous()
+        n = coeffs.numel() // self.N
+        out = self.empty_ct(n) if out is None else out
+        _check(self.lib.bfhe_encrypt_poly(self.h, _ptr(coeffs), n, seed, _ptr(out), self.stream))
+        return out
+
+    def decrypt_poly(self, ct, out=None):
+        n = self._n(ct)
+        out = torch.empty(n, self.N, dtype=torch.int64, device=self.device) if out is None else out
+        _check(self.lib.bfhe_decrypt_poly(self.h, _ptr(ct), n, _ptr(out), self.stream))
         return out
 
     def decrypt(self, ct, out=None):

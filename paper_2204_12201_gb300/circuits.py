@@ -27,7 +27,9 @@ Netlists (the same structure the tests' oracle circuits follow):
 * equality: XNOR per bit (1 - (x + y - 2xy)), then a balanced product tree
   (low half [0, n/2) times high half);
 * increment by the public 1: bit 0 = NOT x_0, carry x_0, then half adders,
-  top carry dropped.
+  top carry dropped;
+* at t = 2 (no batching) XOR = x + y and XNOR = 1 - (x + y) are linear, so
+  the half adders' sums and the equality's XNORs take no multiply.
 
 Fibonacci (Listings 3 and 4): max_iter rounds of r += (i++ == in) * a;
 swap(a, b); a += b, with the initial values as input wires.  Bit-level: a,
@@ -50,7 +52,8 @@ def lin_code(cc, cx, cy, cz):
 
 
 class Netlist:
-    def __init__(self):
+    def __init__(self, t=65537):
+        self.t = t             # plaintext modulus: at t = 2 XOR and XNOR are linear (Sec. 3.1)
         self.n_inputs = 0
         self.nodes = []        # (kind, args) ; node i is wire n_inputs + i (inputs are declared first)
 
@@ -81,9 +84,16 @@ class Netlist:
         return self.lin([(x, -1)], 1)
 
     def half_adder(self, x, y):
-        """(x XOR y, x AND y) sharing one product."""
+        """(x XOR y, x AND y) sharing one product (at t = 2 the sum does not use it)."""
         p = self.mul(x, y)
+        if self.t == 2:
+            return self.lin([(x, 1), (y, 1)]), p
         return self.lin([(x, 1), (y, 1), (p, -2)]), p
+
+    def XOR(self, x, y):
+        if self.t == 2:
+            return self.lin([(x, 1), (y, 1)])
+        return self.half_adder(x, y)[0]
 
     def MUX(self, s, x, y):
         d = self.lin([(x, 1), (y, -1)])
@@ -113,10 +123,7 @@ class Netlist:
             if hi - lo == 1:
                 na = self.NOT(a[lo])
                 lt = self.mul(na, b[lo])
-                eq = None
-                if need_eq:
-                    u, _ = self.half_adder(a[lo], b[lo])
-                    eq = self.NOT(u)
+                eq = self.XNOR(a[lo], b[lo]) if need_eq else None
                 return lt, eq
             mid = lo + (hi - lo) // 2
             lt_l, eq_l = block(lo, mid, need_eq)
@@ -136,6 +143,8 @@ class Netlist:
         return acc
 
     def XNOR(self, x, y):
+        if self.t == 2:
+            return self.lin([(x, -1), (y, -1)], 1)
         p = self.mul(x, y)
         return self.lin([(x, -1), (y, -1), (p, 2)], 1)
 
@@ -229,6 +238,8 @@ class Compiled:
     """A netlist's level tables on the device, runnable eagerly or as a CUDA graph."""
 
     def __init__(self, ctx, net, n):
+        if net.t != ctx.t:
+            raise ValueError("netlist built for t = %d, context has t = %d" % (net.t, ctx.t))
         self.ctx, self.net, self.n = ctx, net, n
         self.calls = []      # (table tensor, n_gates, n_mul)
         for _, muls, subs in net.schedule():

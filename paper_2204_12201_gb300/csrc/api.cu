@@ -250,24 +250,16 @@ extern "C" int bfhe_export_keys(bfhe_ctx* c, int64_t* sk, uint64_t* pk, uint64_t
     return BFHE_OK;
 }
 
-extern "C" int bfhe_encrypt(bfhe_ctx* c, const uint64_t* slots, size_t n, uint64_t seed, uint64_t* ct_out,
-                            void* stream) {
-    CHECK_CTX(c);
-    CHECK_KEYS(c);
-    if (n == 0) return BFHE_OK;
-    if (!slots || !ct_out) return set_error(BFHE_EINVAL, "null buffer");
+namespace {
+
+// (Delta M + pk0 u + e1, pk1 u + e2) for plaintext polynomials M [n][N] (coefficients < t);
+// scratch: u/e1/e2 [3][n][N], U [n][L][N]
+int encrypt_core(bfhe_ctx* c, const u64* M, size_t n, uint64_t seed, u64* ct_out, u64* scratch, cudaStream_t st) {
     const size_t N = c->N, L = c->L;
-    cudaStream_t st = S(stream);
-    // scratch: M[n][N], u/e1/e2 [3][n][N], U[n][L][N]
-    void* p;
-    RC(ctx_scratch(c, (4 * n * N + n * L * N) * sizeof(u64), &p));
-    u64* M = (u64*)p;
-    i64* u = (i64*)(M + n * N);
+    i64* u = (i64*)scratch;
     i64* e1 = u + n * N;
     i64* e2 = e1 + n * N;
     u64* U = (u64*)(e2 + n * N);
-    RC(launch_permute(c, slots, M, (int)n, 1, st));
-    RC(launch_ntt_inv(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), 0, st));
     RC(launch_sample_small(c, u, (int)n, seed, P_ENC_U, 0, 0, st));
     RC(launch_sample_small(c, e1, (int)n, seed, P_ENC_E1, 0, 1, st));
     RC(launch_sample_small(c, e2, (int)n, seed, P_ENC_E2, 0, 1, st));
@@ -280,17 +272,9 @@ extern "C" int bfhe_encrypt(bfhe_ctx* c, const uint64_t* slots, size_t n, uint64
     return BFHE_OK;
 }
 
-extern "C" int bfhe_decrypt(bfhe_ctx* c, const uint64_t* ct, size_t n, uint64_t* slots_out, void* stream) {
-    CHECK_CTX(c);
-    CHECK_KEYS(c);
-    if (n == 0) return BFHE_OK;
-    if (!ct || !slots_out) return set_error(BFHE_EINVAL, "null buffer");
+// M [n][N] = [round(t [c0 + c1 s]_Q / Q)]_t; scratch V [n][L][N]
+int decrypt_core(bfhe_ctx* c, const u64* ct, size_t n, u64* M, u64* V, cudaStream_t st) {
     const size_t N = c->N, L = c->L;
-    cudaStream_t st = S(stream);
-    void* p;
-    RC(ctx_scratch(c, (n * L * N + n * N) * sizeof(u64), &p));
-    u64* V = (u64*)p;
-    u64* M = V + n * L * N;
     NttIO io;
     io.in = ct + L * N;
     io.out = V;
@@ -306,9 +290,72 @@ extern "C" int bfhe_decrypt(bfhe_ctx* c, const uint64_t* ct, size_t n, uint64_t*
     RC(launch_pointwise(c, V, c->d_sk_ntt, V, (int)n, 1, (int)L, c->mapQ(), s, st));
     RC(launch_ntt_inv(c, ntt_io(V, V, L, N), (int)n, (int)L, c->mapQ(), 1, st));
     RC(launch_dec_finish(c, V, ct, M, (int)n, st));
+    return BFHE_OK;
+}
+
+}  // namespace
+
+#define CHECK_BATCHING(ctx)                                                                      \
+    do {                                                                                         \
+        if (!(ctx)->batching)                                                                    \
+            return set_error(BFHE_EINVAL, "no slot encoding at t = 2: use the coefficient calls"); \
+    } while (0)
+
+extern "C" int bfhe_encrypt(bfhe_ctx* c, const uint64_t* slots, size_t n, uint64_t seed, uint64_t* ct_out,
+                            void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    CHECK_BATCHING(c);
+    if (n == 0) return BFHE_OK;
+    if (!slots || !ct_out) return set_error(BFHE_EINVAL, "null buffer");
+    const size_t N = c->N, L = c->L;
+    cudaStream_t st = S(stream);
+    // scratch: M[n][N], u/e1/e2 [3][n][N], U[n][L][N]
+    void* p;
+    RC(ctx_scratch(c, (4 * n * N + n * L * N) * sizeof(u64), &p));
+    u64* M = (u64*)p;
+    RC(launch_permute(c, slots, M, (int)n, 1, st));
+    RC(launch_ntt_inv(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), 0, st));
+    return encrypt_core(c, M, n, seed, ct_out, M + n * N, st);
+}
+
+extern "C" int bfhe_encrypt_poly(bfhe_ctx* c, const uint64_t* coeffs, size_t n, uint64_t seed, uint64_t* ct_out,
+                                 void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!coeffs || !ct_out) return set_error(BFHE_EINVAL, "null buffer");
+    void* p;
+    RC(ctx_scratch(c, (3 * n * c->N + n * c->L * c->N) * sizeof(u64), &p));
+    return encrypt_core(c, coeffs, n, seed, ct_out, (u64*)p, S(stream));
+}
+
+extern "C" int bfhe_decrypt(bfhe_ctx* c, const uint64_t* ct, size_t n, uint64_t* slots_out, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    CHECK_BATCHING(c);
+    if (n == 0) return BFHE_OK;
+    if (!ct || !slots_out) return set_error(BFHE_EINVAL, "null buffer");
+    const size_t N = c->N, L = c->L;
+    cudaStream_t st = S(stream);
+    void* p;
+    RC(ctx_scratch(c, (n * L * N + n * N) * sizeof(u64), &p));
+    u64* V = (u64*)p;
+    u64* M = V + n * L * N;
+    RC(decrypt_core(c, ct, n, M, V, st));
     RC(launch_ntt_fwd(c, ntt_io(M, M, 1, N), (int)n, 1, c->mapT(), st));
     RC(launch_permute(c, M, slots_out, (int)n, 0, st));
     return BFHE_OK;
+}
+
+extern "C" int bfhe_decrypt_poly(bfhe_ctx* c, const uint64_t* ct, size_t n, uint64_t* coeffs_out, void* stream) {
+    CHECK_CTX(c);
+    CHECK_KEYS(c);
+    if (n == 0) return BFHE_OK;
+    if (!ct || !coeffs_out) return set_error(BFHE_EINVAL, "null buffer");
+    void* p;
+    RC(ctx_scratch(c, n * c->L * c->N * sizeof(u64), &p));
+    return decrypt_core(c, ct, n, coeffs_out, (u64*)p, S(stream));
 }
 
 static int lin(bfhe_ctx* c, u64* out, const u64* x, const u64* y, LinCoef cf, u64 cval, size_t n, void* stream) {
@@ -358,6 +405,7 @@ extern "C" int bfhe_mul_scalar(bfhe_ctx* c, const uint64_t* a, uint64_t k, uint6
 extern "C" int bfhe_mul_plain(bfhe_ctx* c, const uint64_t* a, const uint64_t* plain, uint64_t* out, size_t n,
                               void* stream) {
     CHECK_CTX(c);
+    CHECK_BATCHING(c);
     if (n == 0) return BFHE_OK;
     if (!a || !plain || !out) return set_error(BFHE_EINVAL, "null buffer");
     const size_t N = c->N, L = c->L;
@@ -412,6 +460,14 @@ extern "C" int bfhe_bit_gate(bfhe_ctx* c, int gate, const uint64_t* x, const uin
     const size_t ctw = c->ct_words();
     if (gate == BFHE_NOT) {
         RC(launch_lincomb(c, out, x, nullptr, nullptr, nullptr, kGate[gate], 1, n, st));
+    } else if (c->t == 2 && (gate == BFHE_XOR || gate == BFHE_XNOR)) {
+        // mod 2 the XOR equation is x + y; XNOR = 1 - (x + y)
+        const bool xnor = gate == BFHE_XNOR;
+        RC(launch_lincomb(c, out, x, y, nullptr, nullptr,
+                          xnor ? LinCoef{1, -1, -1, 0, 0} : LinCoef{0, 1, 1, 0, 0}, 1, n, st));
+        c->counts[0] += n;
+        if (xnor) c->counts[1] += n;
+        return BFHE_OK;
     } else {
         CHECK_KEYS(c);
         if (out == x || out == y || out == z) return set_error(BFHE_EINVAL, "out must not alias an input");

@@ -124,6 +124,7 @@ struct bfhe_ctx {
     int device = 0;
     uint32_t N = 0, logN = 0, L = 0, alpha = 0, K = 0, nP = 0, prime_bits = 0;
     u64 t = 0;
+    bool batching = true;   // t = 1 mod 2N: slot encoding; t = 2: coefficient encoding only
     std::vector<u64> primes;     // nP: Q, P, B, t
     std::vector<uint32_t> brv;   // host copy of bit reversal (N)
 

@@ -326,8 +326,9 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     const uint32_t bits = prm->prime_bits ? prm->prime_bits : 50;
     if (bits < 30 || bits > 59) return set_error(BFHE_EINVAL, "prime_bits must be in [30, 59]");
     const u64 t = prm->t;
-    if (t < 3 || t >= ((u64)1 << 32) || !is_prime(t) || (t - 1) % (2 * (u64)N) != 0)
-        return set_error(BFHE_EINVAL, "t must be a prime < 2^32 with t = 1 mod 2N");
+    const bool batching = t != 2;
+    if (batching && (t < 3 || t >= ((u64)1 << 32) || !is_prime(t) || (t - 1) % (2 * (u64)N) != 0))
+        return set_error(BFHE_EINVAL, "t must be 2 or a prime < 2^32 with t = 1 mod 2N");
 
     bfhe_ctx* c = new bfhe_ctx();
     c->device = device;
@@ -338,6 +339,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->alpha = prm->alpha;
     c->prime_bits = bits;
     c->t = t;
+    c->batching = batching;
 
     // primes: data, special, then grow the auxiliary base until B > 2 t N Q (B, Q as exact logs)
     const int head = (int)(c->L + c->alpha);
@@ -413,6 +415,11 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2), twist((size_t)nP * 2 * N * 2);
     for (uint32_t p = 0; p < nP; ++p) {
         const u64 q = c->primes[p];
+        if (p == nP - 1 && !batching) {
+            // t = 2: no slot transform; its table rows stay zero and are never read
+            mu[p] = (u64)(((u128)1 << 64) / q);
+            continue;
+        }
         u64 x = q;   // Newton: q * x = 1 mod 2^64
         for (int it = 0; it < 6; ++it) x *= 2 - q * x;
         qinv[p] = (u64)0 - x;

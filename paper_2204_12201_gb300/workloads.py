@@ -81,7 +81,7 @@ class FibonacciJob:
     def __init__(self, ctx, kind, width=8, max_iter=10, n=1):
         assert kind in ("bits", "bridged")
         self.ctx, self.kind, self.width, self.max_iter, self.n = ctx, kind, width, max_iter, n
-        net = circuits.Netlist()
+        net = circuits.Netlist(ctx.t)
         inp, i0 = net.inputs(width), net.inputs(width)
         if kind == "bits":
             a0, b0, r0 = (net.inputs(width) for _ in range(3))
@@ -95,16 +95,24 @@ class FibonacciJob:
         self.circ = circuits.Compiled(ctx, net, n)
 
     def input_slots(self, vals):
-        """vals: device int64 [n][N] inputs -> slot values of every input wire [n_inputs][n][N]."""
+        """vals: device int64 [n][N] inputs -> slot values of every input wire [n_inputs][n][N].
+        Without batching (t = 2) vals is [n][1] and each value sits in coefficient 0 of its
+        plaintext polynomial (the other coefficients zero)."""
         import torch
         planes = torch.stack([(vals >> k) & 1 for k in range(self.width)])
         c = torch.tensor(self.consts, dtype=torch.int64, device=vals.device).view(-1, 1, 1)
-        return torch.cat([planes, c.expand(-1, vals.shape[0], vals.shape[1])])
+        out = torch.cat([planes, c.expand(-1, vals.shape[0], vals.shape[1])])
+        if not self.ctx.batching:
+            poly = torch.zeros(out.shape[0], out.shape[1], self.ctx.N, dtype=torch.int64, device=vals.device)
+            poly[:, :, :1] = out[:, :, :1]
+            out = poly
+        return out
 
     def set_inputs(self, vals, seed):
-        slots = self.input_slots(vals)
-        cts = self.ctx.encrypt(slots.reshape(-1, self.ctx.N), seed)
-        self.circ.set_inputs(cts.view(slots.shape[0], self.n, 2, self.ctx.L, self.ctx.N))
+        slots = self.input_slots(vals).reshape(-1, self.ctx.N)
+        enc = self.ctx.encrypt if self.ctx.batching else self.ctx.encrypt_poly
+        cts = enc(slots, seed)
+        self.circ.set_inputs(cts.view(-1, self.n, 2, self.ctx.L, self.ctx.N))
 
     def run(self):
         self.circ.run()
@@ -114,9 +122,13 @@ class FibonacciJob:
         return self.circ.out(self.out_wires)
 
     def decrypt(self):
-        """Decrypted r per slot: [n][N] (bits recombined for the bit-level program)."""
+        """Decrypted r per slot: [n][N] (bits recombined for the bit-level program); without
+        batching [n][1], coefficient 0."""
         out = self.result()
-        d = [self.ctx.decrypt(out[k].contiguous()) for k in range(out.shape[0])]
+        if self.ctx.batching:
+            d = [self.ctx.decrypt(out[k].contiguous()) for k in range(out.shape[0])]
+        else:
+            d = [self.ctx.decrypt_poly(out[k].contiguous())[:, :1] for k in range(out.shape[0])]
         if self.kind == "bridged":
             return d[0]
         return sum(dk << k for k, dk in enumerate(d))

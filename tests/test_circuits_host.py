@@ -12,7 +12,6 @@ import random
 
 import pytest
 
-from oracle import bridge
 from oracle import circuits as ocirc
 from paper_2204_12201_gb300 import bfhe, circuits
 from tests.test_oracle_bridge import PlainEvaluator, _bits, _fib_oblivious, _val
@@ -57,36 +56,38 @@ def test_lin_code_round_trip():
                     assert code & 0xFF == bfhe.OP_LIN and decode_lin(code) == (cc, cx, cy, cz)
 
 
+@pytest.mark.parametrize("t", [T, 2])
 @pytest.mark.parametrize("width,max_iter", [(4, 10), (4, 20), (8, 10)])
-def test_fibonacci_netlists_plain(width, max_iter):
+def test_fibonacci_netlists_plain(width, max_iter, t):
     vals = list(range(1 << width))
     n = len(vals)
     zero, one = [0] * n, [1] * n
     want = [_fib_oblivious(v, max_iter, width) for v in vals]
 
-    net = circuits.Netlist()
+    net = circuits.Netlist(t)
     inp, i0, a0, b0, r0 = (net.inputs(width) for _ in range(5))
     out = net.fibonacci_bits(inp, i0, a0, b0, r0, max_iter)
     ins = _bits(vals, width) + [zero] * (2 * width) + [one] + [zero] * (2 * width - 1)
-    w = run_plain(net, ins)
+    w = run_plain(net, ins, t)
     assert _val([w[k] for k in out]) == [v % (1 << width) for v in want]
-    ev = PlainEvaluator(T, n)
+    ev = PlainEvaluator(t, n)
     ocirc.fibonacci_bits(ev, _bits(vals, width), [zero] * width, [zero] * width,
                          [one] + [zero] * (width - 1), [zero] * width, max_iter)
     assert net.n_mul == ev.n_mul
 
-    net = circuits.Netlist()
+    net = circuits.Netlist(t)
     inp, i0 = net.inputs(width), net.inputs(width)
     a0, b0, r0 = net.inputs(3)
     out = net.fibonacci_bridged(inp, i0, a0, b0, r0, max_iter)
-    w = run_plain(net, _bits(vals, width) + [zero] * width + [zero, one, zero])
-    assert w[out] == [v % T for v in want]
-    ev = PlainEvaluator(T, n)
+    w = run_plain(net, _bits(vals, width) + [zero] * width + [zero, one, zero], t)
+    assert w[out] == [v % t for v in want]
+    ev = PlainEvaluator(t, n)
     ocirc.fibonacci_bridged(ev, _bits(vals, width), [zero] * width, zero, one, zero, max_iter)
     assert net.n_mul == ev.n_mul
 
 
-def test_arith_netlists_plain():
+@pytest.mark.parametrize("t", [T, 2])
+def test_arith_netlists_plain(t):
     rng = random.Random(13)
     m = 200
     a = [rng.randrange(256) for _ in range(m)]
@@ -100,11 +101,11 @@ def test_arith_netlists_plain():
             (lambda net, x, y: net.increment(x), lambda p, q: (p + 1) % 256,
              lambda ev, x, y: ocirc.increment(ev, x)),
             (lambda net, x, y: net.multiply(x, y), lambda p, q: p * q, ocirc.multiply)):
-        net = circuits.Netlist()
+        net = circuits.Netlist(t)
         x, y = net.inputs(8), net.inputs(8)
         out = build(net, x, y)
-        w = run_plain(net, _bits(a, 8) + _bits(b, 8))
+        w = run_plain(net, _bits(a, 8) + _bits(b, 8), t)
         assert _val([w[k] for k in out]) == [ref(p, q) for p, q in zip(a, b)]
-        ev = PlainEvaluator(T, m)
+        ev = PlainEvaluator(t, m)
         oref(ev, _bits(a, 8), _bits(b, 8))
         assert net.n_mul == ev.n_mul
