@@ -234,6 +234,44 @@ def extras(torch, bfhe, circuits, ctx16):
         del comp
     ctx8.close()
     out["modmul_probe_per_s"] = bfhe.probe_modmul(torch.cuda.current_device())
+    # Fibonacci (Listings 3 and 4), 8-bit words, 10 iterations, one input per slot, at the paper's
+    # ring degree N = 32768 with 16 data primes: bit-level vs bridged
+    from paper_2204_12201_gb300 import workloads
+    ctx32 = bfhe.Context(N=32768, L=16, alpha=1)
+    ctx32.keygen(4)
+    vals = torch.randint(0, 12, (1, 32768), generator=rng, dtype=torch.int64).cuda()
+    fib = [0, 1]
+    while len(fib) < 10:
+        fib.append(fib[-1] + fib[-2])
+    fib += [0, 0]                      # inputs 10 and 11 are never reached in 10 iterations
+    want = torch.tensor(fib, dtype=torch.int64, device="cuda")[vals]
+    fo = {}
+    for kind in ("bits", "bridged"):
+        job = workloads.FibonacciJob(ctx32, kind, 8, 10)
+        job.set_inputs(vals, 12)
+        ms_e = timed(job.run, 2)
+        ok = bool(torch.equal(job.decrypt(), want))
+        job.circ.capture()
+        ms_gr = timed(job.circ.replay, 2)
+        fo[kind] = {"ms_eager": round(ms_e, 2), "ms_graph": round(ms_gr, 2), "mul_relin": job.net.n_mul,
+                    "mul_levels": job.circ.depth, "instances_per_run": 32768, "decrypts_correctly": ok}
+        del job
+    ctx32.close()
+    # the same bit-level program at t = 2 (no batching: one instance per ciphertext, XOR free)
+    ctx2 = bfhe.Context(N=32768, L=16, alpha=1, t=2)
+    ctx2.keygen(4)
+    job = workloads.FibonacciJob(ctx2, "bits", 8, 10, n=1)
+    job.set_inputs(vals[:, :1].contiguous(), 12)
+    ms_e = timed(job.run, 2)
+    ok = bool(torch.equal(job.decrypt(), want[:, :1]))
+    job.circ.capture()
+    ms_gr = timed(job.circ.replay, 2)
+    fo["bits_t2"] = {"ms_eager": round(ms_e, 2), "ms_graph": round(ms_gr, 2), "mul_relin": job.net.n_mul,
+                     "mul_levels": job.circ.depth, "instances_per_run": 1, "decrypts_correctly": ok}
+    del job
+    ctx2.close()
+    fo["bridged_speedup_graph"] = round(fo["bits"]["ms_graph"] / fo["bridged"]["ms_graph"], 2)
+    out["fibonacci_n32768_l16_8bit_10iter"] = fo
     # serving: a Poisson stream of mixed requests (N in {4096, 8192, 16384}, 1..16 squarings,
     # 1..64 ciphertexts), continuous batching vs one request at a time with per-op launches
     from paper_2204_12201_gb300 import serving
