@@ -392,7 +392,8 @@ def main():
                                % (props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0), src),
                 "avg_launch_ms": d_ms / max(1, d_launch), "launches": d_launch,
                 "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 3)
-                                 for k, v in prof.items()}}
+                                 for k, v in prof.items()},
+                "kernel_alu_frac": {k: round(v[2] / (v[0] / 1e3) / peak, 3) for k, v in prof.items() if v[0] > 0}}
 
     ext = {} if args.no_extras else extras(torch, bfhe, circuits, ctx)
     if rank == 0:

@@ -57,7 +57,7 @@ typedef struct {
     uint32_t N;          /* ring degree, power of two, 1024 .. 32768          */
     uint32_t L;          /* data primes, 1 .. 16                               */
     uint32_t alpha;      /* special primes, 1 or 2                             */
-    uint32_t prime_bits; /* bit size of every modulus, 30 .. 60 (default 50)   */
+    uint32_t prime_bits; /* bit size of every modulus, 30 .. 58 (default 50)   */
     uint64_t t;          /* plaintext modulus: a prime = 1 (mod 2N), < 2^32,   */
                          /* or 2 (no batching: coefficient encoding only,      */
                          /* Sec. 4.1 and 4.3 run bit-level arithmetic at t = 2) */

@@ -56,6 +56,16 @@ __host__ __device__ __forceinline__ u64 shoup_lazy3(u64 a, u64 w, u64 ws, u64 q)
     return a * w - hi * q;
 }
 
+// a * w mod q in [0, 4q) for a < 2^64: the quotient estimate keeps a1 w1 and the high
+// halves of the two cross products a1 w0, a0 w1 (their low halves and a0 w0 together are
+// below 3 2^64), so it is floor(a ws / 2^64) minus 0, 1 or 2, and Shoup's own estimate
+// is the true quotient or one less.
+__host__ __device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 ws, u64 q) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), w0 = (uint32_t)ws, w1 = (uint32_t)(ws >> 32);
+    const u64 hi = (u64)a1 * w1 + (((u64)a1 * w0) >> 32) + (((u64)a0 * w1) >> 32);
+    return a * w - hi * q;
+}
+
 __host__ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
     u64 r = shoup_lazy(a, w, ws, q);
     return r >= q ? r - q : r;

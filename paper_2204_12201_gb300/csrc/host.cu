@@ -324,7 +324,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     if (prm->L < 1 || prm->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "L must be in [1, 16]");
     if (prm->alpha < 1 || prm->alpha > BFHE_MAX_ALPHA) return set_error(BFHE_EINVAL, "alpha must be 1 or 2");
     const uint32_t bits = prm->prime_bits ? prm->prime_bits : 50;
-    if (bits < 30 || bits > 59) return set_error(BFHE_EINVAL, "prime_bits must be in [30, 59]");
+    if (bits < 30 || bits > 58) return set_error(BFHE_EINVAL, "prime_bits must be in [30, 58]");   // NTT bound 64q <= 2^64
     const u64 t = prm->t;
     const bool batching = t != 2;
     if (batching && (t < 3 || t >= ((u64)1 << 32) || !is_prime(t) || (t - 1) % (2 * (u64)N) != 0))

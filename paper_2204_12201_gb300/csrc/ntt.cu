@@ -3,11 +3,11 @@
 // Forward: Cooley-Tukey with merged psi twiddles (natural order in, bit-
 // reversed evaluation order out); butterfly on bit b of the index with
 // twiddle psi^brv((N + j) >> (b + 1)) and one Shoup product.  The forward
-// butterfly (X, Y) -> (X + T, X - T + 3q), T = Shoup(Y) in [0, 3q) (the
-// quotient estimate may be one short, see shoup_lazy3), grows the bound by 3q
-// per stage and is never reduced in between: from inputs < 4q, 15 stages stay
-// below 49q < 2^56 for q < 2^50, and one Barrett-style reduction at the end
-// makes the output canonical.  Inverse: a_m = N^-1 psi^-m sum_k a^_k
+// butterfly (X, Y) -> (X + T, X - T + 4q), T = Shoup(Y) in [0, 4q) (the
+// quotient estimate may be up to three short, see shoup_lazy4), grows the
+// bound by 4q per stage and is never reduced in between: from inputs < 4q,
+// 15 stages stay below 64q <= 2^64 for q < 2^58, and one Barrett-style
+// reduction at the end makes the output canonical.  Inverse: a_m = N^-1 psi^-m sum_k a^_k
 // omega^-km (omega = psi^2) -- a cyclic decimation-in-time transform on the
 // bit-reversed input with the same reduction-free butterfly, then one twist
 // product by N^-1 psi^-m per word (times R = 2^64 when the inputs carry a
@@ -79,7 +79,7 @@ __device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx) {
 template <int LOG_E, int W_LO, int HI, int LO>
 __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q3 = 3 * q;
+    const u64 q4 = 4 * q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = HI - st;
@@ -93,9 +93,9 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
                 const u64 X = x[e];
-                const u64 T = shoup_lazy3(x[e2], wp.x, wp.y, q);
+                const u64 T = shoup_lazy4(x[e2], wp.x, wp.y, q);
                 x[e] = X + T;
-                x[e2] = X + q3 - T;
+                x[e2] = X + q4 - T;
             }
         }
     }
@@ -116,12 +116,12 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
     if (P == 0) {
         if (TOP) {
             const ulonglong2 w1 = __ldg(tw + 1);
-            const u64 q3 = 3 * q;
+            const u64 q4 = 4 * q;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const u64 X = in[base + (e << W_LO)];
-                const u64 T = shoup_lazy3(in[M + base + (e << W_LO)], w1.x, w1.y, q);
-                x[e] = half ? X + q3 - T : X + T;
+                const u64 T = shoup_lazy4(in[M + base + (e << W_LO)], w1.x, w1.y, q);
+                x[e] = half ? X + q4 - T : X + T;
             }
             // both halves of the limb are read before either CTA writes (in-place transforms)
             cg::this_cluster().sync();
@@ -164,13 +164,13 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 ? 2 : 1)) k_
 
 // ---------------------------------------------------------------- inverse stages
 // Decimation in time on the bit-reversed input with inverse roots: the butterfly on
-// bit b at lower index x is (U, V) -> (U + T, U - T + 3q), T = V omega^-(N/2^(b+1)) (x mod 2^b)
-// (table entry 2^b + (x mod 2^b)); bounds grow by 3q per stage, as in the forward.
+// bit b at lower index x is (U, V) -> (U + T, U - T + 4q), T = V omega^-(N/2^(b+1)) (x mod 2^b)
+// (table entry 2^b + (x mod 2^b)); bounds grow by 4q per stage, as in the forward.
 // The natural-order output is then multiplied by the twist N^-1 psi^-m.
 template <int LOG_E, int W_LO, int LO, int HI>
 __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const ulonglong2* __restrict__ itw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q3 = 3 * q;
+    const u64 q4 = 4 * q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = LO + st;
@@ -184,9 +184,9 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
                 const u64 U = x[e];
-                const u64 T = shoup_lazy3(x[e2], wp.x, wp.y, q);
+                const u64 T = shoup_lazy4(x[e2], wp.x, wp.y, q);
                 x[e] = U + T;
-                x[e2] = U + q3 - T;
+                x[e2] = U + q4 - T;
             }
         }
     }
@@ -232,15 +232,15 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
         cl.sync();
         const u64* peer = cl.map_shared_rank(sm, cl.block_rank() ^ 1u);
-        const u64 q3 = 3 * q;
+        const u64 q4 = 4 * q;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = base + (e << W_LO);
             const u64 other = peer[phys(j)];
             const u64 U = half ? other : x[e], V = half ? x[e] : other;
             const ulonglong2 wp = __ldg(itw + M + j);
-            const u64 T = shoup_lazy3(V, wp.x, wp.y, q);
-            const u64 y = half ? U + q3 - T : U + T;
+            const u64 T = shoup_lazy4(V, wp.x, wp.y, q);
+            const u64 y = half ? U + q4 - T : U + T;
             const ulonglong2 tw = __ldg(twist + j + half * M);
             out[j] = shoup(y, tw.x, tw.y, q);
         }

@@ -5,10 +5,29 @@ python -m paper_2204_12201_gb300.profile_cases ntt --N 16384 --L 8 --polys 256
     above the 129 MB L2), three rounds; capture with -s 2 -c 2 to skip the first round.
 python -m paper_2204_12201_gb300.profile_cases mul --N 16384 --L 8 --n 32
     three batched mul_relin calls of n ciphertext pairs.
+
+The measured rounds run inside the NVTX range "bfhe_cases", so that ncu can
+skip the set-up (keygen, encryption) with --nvtx --nvtx-include "bfhe_cases/".
 """
 
 import argparse
+import contextlib
 import sys
+
+
+@contextlib.contextmanager
+def _range(torch, name):
+    """An NVTX push/pop range around the measured rounds (a no-op where NVTX is missing)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+        pushed = True
+    except RuntimeError:
+        pushed = False
+    try:
+        yield
+    finally:
+        if pushed:
+            torch.cuda.nvtx.range_pop()
 
 
 def main(argv=None):
@@ -27,9 +46,11 @@ def main(argv=None):
     ctx = bfhe.Context(N=a.N, L=a.L, alpha=a.alpha)
     if a.case == "ntt":
         x = torch.randint(0, 1 << 40, (a.polys, a.L, a.N), dtype=torch.int64, device="cuda")
-        for _ in range(a.rounds):
-            ctx.ntt(x)
-            ctx.ntt(x, inverse=True)
+        torch.cuda.synchronize()
+        with _range(torch, "bfhe_cases"):
+            for _ in range(a.rounds):
+                ctx.ntt(x)
+                ctx.ntt(x, inverse=True)
     else:
         ctx.keygen(1)
         g = torch.Generator().manual_seed(3)
@@ -37,8 +58,10 @@ def main(argv=None):
         ct = ctx.encrypt(ys, 5)
         x, y = ct[: a.n].contiguous(), ct[a.n:].contiguous()
         out = torch.empty_like(x)
-        for _ in range(a.rounds):
-            ctx.mul_relin(x, y, out=out)
+        torch.cuda.synchronize()
+        with _range(torch, "bfhe_cases"):
+            for _ in range(a.rounds):
+                ctx.mul_relin(x, y, out=out)
     torch.cuda.synchronize()
     ctx.close()
     print("ok")
