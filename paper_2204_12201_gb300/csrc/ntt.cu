@@ -140,7 +140,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         __syncthreads();
         fwd_pass<LOG_M, LOG_E, P + 1, TOP>(x, sm, tid, jglob, tw, q, mu, in, out, half);
     } else {
-        // W_LO == 0 here: E consecutive words per thread; values < 49q -> canonical
+        // W_LO == 0 here: E consecutive words per thread; values < 64q -> canonical
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = reduce64(x[e], q, mu);
         ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + base);
@@ -150,7 +150,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 }
 
 template <int LOG_M, int LOG_E, bool TOP>
-__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 ? 2 : 1)) k_ntt_fwd(NttArgs a) {
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 && LOG_M - LOG_E <= 8 ? 2 : 1)) k_ntt_fwd(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
     const int half = blockIdx.y;
@@ -256,7 +256,7 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 }
 
 template <int LOG_M, int LOG_E, int MODE>
-__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14 ? 2 : 1)) k_ntt_inv(NttArgs a) {
+__global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14 && LOG_M - LOG_E <= 8 ? 2 : 1)) k_ntt_inv(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
     const int half = blockIdx.y;
