@@ -45,6 +45,29 @@ CPU_SAMPLE_N = 16384
 
 
 # --------------------------------------------------------------------------- helpers
+def ntt_traffic_per_limb(kernel):
+    """DRAM bytes per limb of the dominant kernel from the committed ncu summary, or None when the
+    kernel's sources changed since those counters were taken (the summary records their hash)."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", "%s_traffic_genotype_N16384.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ("ntt.cu", "common.cuh"):
+        with open(os.path.join(here, "paper_2204_12201_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("- ") and ": " in line:
+                k, v = line[2:].strip().split(": ", 1)
+                fields[k.strip("`")] = v.strip("`")
+    if fields.get("sources_sha256") != h.hexdigest():
+        return None
+    return float(fields["dram_bytes_per_limb"])
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -385,8 +408,14 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     d_ms, d_launch, d_work = prof[dom]
     achieved = d_work / (d_ms / 1e3)
+    traffic = None
+    if dom.startswith("ntt"):
+        per_limb = ntt_traffic_per_limb("k_" + dom)
+        if per_limb is not None:
+            limbs_per_launch = d_work / max(1, d_launch) / (WL["N"] // 2 * (WL["N"].bit_length() - 1))
+            traffic = per_limb * limbs_per_launch
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "modmul/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": "derived: %d SMs x 64 IMAD/clk x %.0f MHz / 16 IMAD slots per 64-bit "
                                "Shoup product (clock from MEASURED_PEAKS.json, %s)"
                                % (props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0), src),

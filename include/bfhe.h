@@ -77,6 +77,18 @@ int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out);
  * growth, hence device synchronisation, inside later calls). */
 int bfhe_reserve(bfhe_ctx* ctx, size_t n);
 
+/* Process-wide device-memory budget for one call's scratch (default 16 GiB).
+ * Calls whose batch needs more are tiled: the multiplies run in chunks that
+ * fit, mod_to_bits runs its candidates in groups; results do not depend on
+ * the budget.  A smaller budget bounds the arena for memory-constrained
+ * serving (and lets tests run the tiled paths at small sizes).  It is a
+ * target, not a cap: a call always gets its fixed buffers and the scratch of
+ * one multiply.  Budgets below 1 MiB are rejected (BFHE_EINVAL).  Not
+ * synchronised with calls in flight on other host threads: set it before
+ * using the library. */
+int bfhe_set_scratch_budget(size_t bytes);
+size_t bfhe_scratch_budget(void);
+
 /* Key generation from `seed` (keys stay resident on the device): secret s
  * ternary, pk = ([-(a s + e)]_Q, a), relinearisation keys for the RNS digits
  * j = 0..L-1: ([-(a_j s + e_j) + P g_j s^2]_{PQ}, a_j), g_j = (Q/q_j)

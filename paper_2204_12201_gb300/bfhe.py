@@ -70,6 +70,8 @@ def load():
         "bfhe_profile_read": (I, [P, P, P, P]),
         "bfhe_probe_modmul": (I, [I, U32, P, P]),
         "bfhe_launch_count": (ctypes.c_uint64, []),
+        "bfhe_set_scratch_budget": (I, [S]),
+        "bfhe_scratch_budget": (S, []),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
         "bfhe_last_error": (ctypes.c_char_p, []),
@@ -186,9 +188,16 @@ class Context:
         _check(self.lib.bfhe_decrypt(self.h, _ptr(ct), n, _ptr(out), self.stream))
         return out
 
+    def _same(self, n, *cts):
+        """Every buffer holds n ciphertexts (checked before the library reads or writes them)."""
+        for c in cts:
+            if c is not None and self._n(c) != n:
+                raise ValueError("batch sizes differ: %d vs %d ciphertexts" % (self._n(c), n))
+
     def _binary(self, fn, a, b, out):
         n = self._n(a)
         out = torch.empty_like(a) if out is None else out
+        self._same(n, b, out)
         _check(fn(self.h, _ptr(a), _ptr(b), _ptr(out), n, self.stream))
         return out
 
@@ -206,30 +215,42 @@ class Context:
         return self._binary(self.lib.bfhe_mul_relin_noalloc, a, b, out)
 
     def mul_plain(self, a, plain, out=None):
-        return self._binary(self.lib.bfhe_mul_plain, a, plain.contiguous(), out)
+        n = self._n(a)
+        plain = plain.contiguous()
+        if plain.numel() != n * self.N:
+            raise ValueError("plain holds %d words, want %d slot vectors of %d" % (plain.numel(), n, self.N))
+        out = torch.empty_like(a) if out is None else out
+        self._same(n, out)
+        _check(self.lib.bfhe_mul_plain(self.h, _ptr(a), _ptr(plain), _ptr(out), n, self.stream))
+        return out
 
     def add_const(self, a, c, out=None):
         out = torch.empty_like(a) if out is None else out
+        self._same(self._n(a), out)
         _check(self.lib.bfhe_add_const(self.h, _ptr(a), c, _ptr(out), self._n(a), self.stream))
         return out
 
     def sub_const(self, a, c, out=None):
         out = torch.empty_like(a) if out is None else out
+        self._same(self._n(a), out)
         _check(self.lib.bfhe_sub_const(self.h, _ptr(a), c, _ptr(out), self._n(a), self.stream))
         return out
 
     def const_sub(self, c, a, out=None):
         out = torch.empty_like(a) if out is None else out
+        self._same(self._n(a), out)
         _check(self.lib.bfhe_const_sub(self.h, c, _ptr(a), _ptr(out), self._n(a), self.stream))
         return out
 
     def mul_scalar(self, a, c, out=None):
         out = torch.empty_like(a) if out is None else out
+        self._same(self._n(a), out)
         _check(self.lib.bfhe_mul_scalar(self.h, _ptr(a), c, _ptr(out), self._n(a), self.stream))
         return out
 
     def bit_gate(self, gate, x, y=None, z=None, out=None):
         out = torch.empty_like(x) if out is None else out
+        self._same(self._n(x), y, z, out)
         _check(self.lib.bfhe_bit_gate(self.h, gate, _ptr(x), _ptr(y), _ptr(z), _ptr(out), self._n(x),
                                       self.stream))
         return out
@@ -242,20 +263,25 @@ class Context:
 
     def bits_to_mod(self, bits, out=None):
         s, n = bits.shape[0], bits.shape[1]
+        self._same(s * n, bits)
         out = self.empty_ct(n) if out is None else out
+        self._same(n, out)
         _check(self.lib.bfhe_bits_to_mod(self.h, _ptr(bits), s, _ptr(out), n, self.stream))
         return out
 
     def mod_to_bits(self, x, s, c_lo, c_hi, mode=PAPER, out=None):
         n = self._n(x)
         out = self.empty_ct(n, s) if out is None else out
+        self._same(s * n, out)
         _check(self.lib.bfhe_mod_to_bits(self.h, _ptr(x), s, c_lo, c_hi, mode, _ptr(out), n, self.stream))
         return out
 
     def sint_to_mod(self, bits, out=None):
         """bits [s][n][2][L][N]: two's complement, sign bit last (Listing 6)."""
         s, n = bits.shape[0], bits.shape[1]
+        self._same(s * n, bits)
         out = self.empty_ct(n) if out is None else out
+        self._same(n, out)
         _check(self.lib.bfhe_sint_to_mod(self.h, _ptr(bits), s, _ptr(out), n, self.stream))
         return out
 
@@ -263,12 +289,14 @@ class Context:
         """Listing 9; pos_range / neg_range = (lo, hi) candidates of x and of (2^s - t) + x."""
         n = self._n(x)
         out = self.empty_ct(n, s) if out is None else out
+        self._same(s * n, out)
         _check(self.lib.bfhe_mod_to_sint(self.h, _ptr(x), s, pos_range[0], pos_range[1], neg_range[0],
                                          neg_range[1], mode, _ptr(out), n, self.stream))
         return out
 
     def pow(self, x, e, out=None):
         out = torch.empty_like(x) if out is None else out
+        self._same(self._n(x), out)
         _check(self.lib.bfhe_pow(self.h, _ptr(x), e, _ptr(out), self._n(x), self.stream))
         return out
 
@@ -315,3 +343,12 @@ def ntt_config(logN, inverse, log_m=0, log_e=0):
     m, e = ctypes.c_uint32(), ctypes.c_uint32()
     _check(load().bfhe_ntt_config(logN, int(inverse), log_m, log_e, ctypes.byref(m), ctypes.byref(e)))
     return m.value, e.value
+
+
+def set_scratch_budget(nbytes):
+    """Per-call scratch budget in bytes (process-wide); larger batches are tiled."""
+    _check(load().bfhe_set_scratch_budget(int(nbytes)))
+
+
+def scratch_budget():
+    return int(load().bfhe_scratch_budget())

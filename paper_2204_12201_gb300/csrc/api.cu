@@ -165,6 +165,15 @@ size_t pow_buf_words(const bfhe_ctx* c, u64 e, size_t n) {
 }  // namespace
 
 // ------------------------------------------------------------------ ABI
+extern "C" int bfhe_set_scratch_budget(size_t bytes) {
+    // one multiply at the largest parameters needs far less than 1 MiB x 64; below 1 MiB nothing fits
+    if (bytes < ((size_t)1 << 20)) return set_error(BFHE_EINVAL, "scratch budget below 1 MiB");
+    g_scratch_budget = bytes;
+    return BFHE_OK;
+}
+
+extern "C" size_t bfhe_scratch_budget(void) { return g_scratch_budget; }
+
 extern "C" int bfhe_reserve(bfhe_ctx* c, size_t n) {
     CHECK_CTX(c);
     void* p;

@@ -32,3 +32,47 @@ def test_binding_covers_the_abi():
     src = open(bfhe.__file__).read()
     missing = [n for n in declared() if '"%s"' % n not in src]
     assert not missing, missing
+
+
+def _lib():
+    from paper_2204_12201_gb300 import bfhe
+    path = build.lib_path()
+    if not os.path.exists(path):
+        build.build()
+    return bfhe.load(), bfhe
+
+
+def test_context_parameters_are_validated_on_the_host():
+    """Every rejected parameter set returns BFHE_EINVAL before any CUDA call (runs without a GPU)."""
+    lib, bfhe = _lib()
+    bad = [dict(N=1000), dict(N=512), dict(N=65536), dict(L=0), dict(L=17), dict(alpha=0), dict(alpha=3),
+           dict(prime_bits=29), dict(prime_bits=59), dict(t=65536), dict(t=17), dict(t=3), dict(t=1),
+           dict(t=(1 << 32) + 15)]
+    for over in bad:
+        kw = dict(N=4096, L=2, alpha=1, prime_bits=50, t=65537)
+        kw.update(over)
+        prm = bfhe._Params(kw["N"], kw["L"], kw["alpha"], kw["prime_bits"], kw["t"])
+        out = ctypes.c_void_p(0)
+        rc = lib.bfhe_ctx_create(ctypes.byref(prm), 0, ctypes.byref(out))
+        assert rc == -1, over
+        assert out.value is None, over
+        assert lib.bfhe_last_error().decode()
+
+
+def test_scratch_budget_setting():
+    lib, bfhe = _lib()
+    old = bfhe.scratch_budget()
+    try:
+        with __import__("pytest").raises(bfhe.BfheError):
+            bfhe.set_scratch_budget(1000)
+        bfhe.set_scratch_budget(64 << 20)
+        assert bfhe.scratch_budget() == 64 << 20
+    finally:
+        bfhe.set_scratch_budget(old)
+    assert bfhe.scratch_budget() == old == 16 << 30
+
+
+def test_error_strings():
+    lib, _ = _lib()
+    for rc in (0, -1, -2, -3, -4, -5):
+        assert lib.bfhe_strerror(rc)
