@@ -45,6 +45,22 @@ CPU_SAMPLE_N = 16384
 
 
 # --------------------------------------------------------------------------- helpers
+def base_config():
+    """The workload fields both arms report."""
+    return {"workload": WORKLOAD, "N": WL["N"], "L": WL["L"], "alpha": WL["alpha"], "t": WL["t"]}
+
+
+def combine_ranks(dist, ms, units, device):
+    """Max over ranks of the timed-region duration and the units all ranks processed."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
 def ntt_traffic_per_limb(kernel):
     """DRAM bytes per limb of the dominant kernel from the committed ncu summary, or None when the
     kernel's sources changed since those counters were taken (the summary records their hash)."""
@@ -192,9 +208,11 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (exact)",
             "data": "synthetic",
-            "config": {"workload": "oracle mul_relin at N=16384, L=8, alpha=1 (one per host core per step)"},
+            "config": {**base_config(), "parallelism": "host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": n_procs, "kind": "oracle",
-                             "sample": "%d mul_relin per step, one per process" % n_procs},
+                             "sample": "the step's multiply: %d oracle mul_relin at N=%d, L=%d, alpha=%d per step "
+                                       "(random ciphertexts, random-key stand-in), one per process"
+                                       % (n_procs, CPU_SAMPLE_N, WL["L"], WL["alpha"])},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -378,11 +396,8 @@ def main():
     launches = bfhe.launch_count() - launches0
     clk = clocks.stop()
     n_add, n_sub, n_mul, n_pmul = ctx.op_counts(reset=True)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = n_mul * world / (ms / 1e3)
+    ms, total_mul = combine_ranks(dist, ms, n_mul, "cuda")
+    value = total_mul / (ms / 1e3)
 
     # ---------------- e2e: the same job from host buffers (pinned), copies inside the timed region
     G_h = torch.from_numpy(Gs).pin_memory()
@@ -429,8 +444,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": WL["N"], "L": WL["L"], "alpha": WL["alpha"],
-                           "t": WL["t"], "mul_relin_per_step": n_mul // args.steps,
+                "config": {**base_config(), "mul_relin_per_step": n_mul // args.steps,
                            "parallelism": "replicas" if world > 1 else "single",
                            "ntt_shapes": {k: v["shape"] for k, v in shapes.items()},
                            "l2": "no flush: per-step working set > 10 GB >> 129 MB L2"},
