@@ -76,9 +76,9 @@ def ntt_traffic_per_limb(kernel):
     fields = {}
     with open(path) as fh:
         for line in fh:
-            if line.startswith("- ") and ": " in line:
+            if line.startswith("- `") and ": `" in line:
                 k, v = line[2:].strip().split(": ", 1)
-                fields[k.strip("`")] = v.strip("`")
+                fields[k.strip("`")] = v.split("`")[1]
     if fields.get("sources_sha256") != h.hexdigest():
         return None
     return float(fields["dram_bytes_per_limb"])

@@ -561,15 +561,17 @@ struct M2BPlan {
 M2BPlan m2b_plan(const bfhe_ctx* c, uint32_t s, size_t total, int mode, size_t n, size_t reserve) {
     const size_t ctw = c->ct_words();
     const u64 e = c->t - 1;
-    // candidates per tile: chain buffers (2 + popcount(e)) + PAPER's trivial bits, eq copies and products (3s)
+    // candidates per tile: chain buffers (2 + popcount(e)) + PAPER's trivial bits, eq copies and products (3s),
+    // and the multiply scratch of the tile's squarings in one launch (PAPER's s ANDs per candidate then run
+    // in s chunks of the same size)
     const size_t per_cand = n * ctw * (pow_buf_words(c, e, 1) / ctw + (mode == BFHE_PAPER ? 3 * s : 0) + 2);
-    const size_t mul_per_cand = (mode == BFHE_PAPER ? s : 1) * n * mul_words_per_ct(c);
+    const size_t mul_per_cand = n * mul_words_per_ct(c);
     const size_t budget = g_scratch_budget / sizeof(u64);
     const size_t room = budget > reserve ? budget - reserve : 0;
     size_t C = room / (per_cand + mul_per_cand);
     if (C == 0) C = 1;
     if (C > total) C = total;
-    return {C, reserve + C * per_cand, C * (mode == BFHE_PAPER ? s : 1) * n};
+    return {C, reserve + C * per_cand, C * n};
 }
 
 bool m2b_args_ok(const bfhe_ctx* c, uint32_t s, u64 c_lo, u64 c_hi, int mode) {
