@@ -45,6 +45,17 @@ extern "C" {
 #define BFHE_ETIMEOUT (-4) /* a device-side wait gave up                   */
 #define BFHE_ESTATE (-5)   /* call out of order (e.g. encrypt before keygen) */
 
+/* Input-range flags.  Calls are asynchronous, so values are not checked on
+ * the host; kernels that read a plaintext value (encrypt, encrypt_poly,
+ * mul_plain) or a ciphertext residue (mul_relin and everything built on it,
+ * decrypt) raise a flag in the context when one is out of range, and compute
+ * on regardless (a wrong but in-bounds result: no fault).  bfhe_check
+ * synchronises `stream`, returns the flags raised since the previous check in
+ * *flags_out (may be NULL), clears them, and returns BFHE_EINVAL if any was
+ * raised.  Linear ops (add, sub, ...) do not check. */
+#define BFHE_FLAG_PLAINTEXT 1u   /* a slot value or plaintext coefficient >= t */
+#define BFHE_FLAG_RESIDUE 2u     /* a ciphertext residue >= its prime q_i      */
+
 typedef struct bfhe_ctx bfhe_ctx;
 
 /* Parameters.  The moduli follow one rule (the paper fixes only n, t and the
@@ -72,6 +83,8 @@ void bfhe_ctx_destroy(bfhe_ctx* ctx);
  * p_0..p_{alpha-1}, b_0..b_{K-1} (host buffer of at least 64 entries);
  * *K_out = K.  Also usable before keygen. */
 int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out);
+
+int bfhe_check(bfhe_ctx* ctx, void* stream, uint32_t* flags_out);
 
 /* Reserve scratch for batches of up to n ciphertexts in every call (avoids
  * growth, hence device synchronisation, inside later calls). */

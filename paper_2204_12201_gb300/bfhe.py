@@ -71,6 +71,7 @@ def load():
         "bfhe_probe_modmul": (I, [I, U32, P, P]),
         "bfhe_launch_count": (ctypes.c_uint64, []),
         "bfhe_set_scratch_budget": (I, [S]),
+        "bfhe_check": (I, [P, P, P]),
         "bfhe_scratch_budget": (S, []),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
@@ -143,6 +144,18 @@ class Context:
         return ct.numel() // (2 * self.L * self.N)
 
     # ---------------------------------------------------------------- ABI
+    def check(self):
+        """Synchronise the current stream; raise BfheError if a kernel saw an out-of-range input
+        since the previous check (flags BFHE_FLAG_PLAINTEXT = 1, BFHE_FLAG_RESIDUE = 2)."""
+        f = ctypes.c_uint32(0)
+        rc = self.lib.bfhe_check(self.h, self.stream, ctypes.byref(f))
+        if rc != 0 and f.value == 0:
+            _check(rc)
+        if f.value:
+            err = BfheError("out-of-range input (flags %d): %s" % (f.value, self.lib.bfhe_last_error().decode()))
+            err.flags = f.value
+            raise err
+
     def reserve(self, n):
         _check(self.lib.bfhe_reserve(self.h, n))
 

@@ -165,6 +165,22 @@ size_t pow_buf_words(const bfhe_ctx* c, u64 e, size_t n) {
 }  // namespace
 
 // ------------------------------------------------------------------ ABI
+extern "C" int bfhe_check(bfhe_ctx* c, void* stream, uint32_t* flags_out) {
+    CHECK_CTX(c);
+    uint32_t f = 0;
+    BFHE_CUDA(cudaStreamSynchronize(S(stream)));
+    BFHE_CUDA(cudaMemcpy(&f, c->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
+    BFHE_CUDA(cudaMemset(c->d_flags, 0, sizeof(f)));
+    if (flags_out) *flags_out = f;
+    if (f) {
+        std::string m = "out-of-range input seen on the device:";
+        if (f & BFHE_FLAG_PLAINTEXT) m += " a plaintext value >= t;";
+        if (f & BFHE_FLAG_RESIDUE) m += " a ciphertext residue >= its prime;";
+        return set_error(BFHE_EINVAL, m);
+    }
+    return BFHE_OK;
+}
+
 extern "C" int bfhe_set_scratch_budget(size_t bytes) {
     // one multiply at the largest parameters needs far less than 1 MiB x 64; below 1 MiB nothing fits
     if (bytes < ((size_t)1 << 20)) return set_error(BFHE_EINVAL, "scratch budget below 1 MiB");

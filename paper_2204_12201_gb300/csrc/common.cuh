@@ -160,6 +160,9 @@ struct bfhe_ctx {
     u64* d_pk_ntt = nullptr;     // [2][L][N]
     u64* d_rlk_ntt = nullptr;    // [L][2][L+alpha][N]
 
+    // input-range flags raised by kernels (BFHE_FLAG_*), read and cleared by bfhe_check
+    uint32_t* d_flags = nullptr;
+
     // scratch
     void* scratch = nullptr;
     size_t scratch_bytes = 0;

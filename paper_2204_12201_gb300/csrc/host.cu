@@ -514,6 +514,15 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
         delete c;
         return rc;
     }
+    cudaError_t fe = cudaMalloc(&c->d_flags, 256);
+    if (fe == cudaSuccess) fe = cudaMemset(c->d_flags, 0, 256);
+    if (fe != cudaSuccess) {
+        int rc = cuda_check(fe, "context flags");
+        cudaFree(c->d_arena);
+        if (c->d_flags) cudaFree(c->d_flags);
+        delete c;
+        return rc;
+    }
     const u64* base = (const u64*)c->d_arena;
     c->tab.q = base + o_q;
     c->tab.qinv = base + o_qinv;
@@ -541,6 +550,7 @@ extern "C" void bfhe_ctx_destroy(bfhe_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     cudaFree(ctx->d_arena);
+    cudaFree(ctx->d_flags);
     cudaFree(ctx->scratch);
     cudaFree(ctx->d_sk);
     cudaFree(ctx->d_sk_ntt);

@@ -173,9 +173,12 @@ __global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, in
 
 // key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC).
 // A thread owns one word (k, coefficient) of Q u P: it keeps the 2L key words of that word in
-// registers and walks a group of ciphertexts, so the key is read once per group.
+// registers and walks a group of ciphertexts, so the key is read once per group.  The digits of the
+// next D ciphertexts are in flight while the current one is accumulated (D = 2 while the registers
+// allow two CTAs of 256 threads per SM, else 1).
 template <int L>
 __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, int cpg, PrimeTab tab, int N) {
+    constexpr int D = L <= 8 ? 2 : 1;
     const size_t plane = (size_t)QP * N;
     const int groups = (n + cpg - 1) / cpg;
     const size_t total = plane * groups;
@@ -191,18 +194,34 @@ __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, in
             k0[j] = rlk[((size_t)j * 2 + 0) * plane + off];
             k1[j] = rlk[((size_t)j * 2 + 1) * plane + off];
         }
-        const int c_end = min(n, (grp + 1) * cpg);
-        for (int c = grp * cpg; c < c_end; ++c) {
+        const int c0 = grp * cpg, c_end = min(n, (grp + 1) * cpg);
+        u64 buf[D + 1][L];
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+            if (c0 + b < c_end) {
+                const u64* d = Dg + (size_t)(c0 + b) * L * plane + off;
+#pragma unroll
+                for (int j = 0; j < L; ++j) buf[b][j] = d[(size_t)j * plane];
+            }
+        }
+        for (int c = c0; c < c_end; ++c) {
+            if (c + D < c_end) {
+                const u64* d = Dg + (size_t)(c + D) * L * plane + off;
+#pragma unroll
+                for (int j = 0; j < L; ++j) buf[D][j] = d[(size_t)j * plane];
+            }
             u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
-            const u64* d = Dg + (size_t)c * L * plane + off;
 #pragma unroll
             for (int j = 0; j < L; ++j) {
-                const u64 v = d[(size_t)j * plane];
-                mac128(h0, l0, v, k0[j]);
-                mac128(h1, l1, v, k1[j]);
+                mac128(h0, l0, buf[0][j], k0[j]);
+                mac128(h1, l1, buf[0][j], k1[j]);
             }
             W[((size_t)c * 2 + 0) * plane + off] = redc(h0, l0, q, qinv);
             W[((size_t)c * 2 + 1) * plane + off] = redc(h1, l1, q, qinv);
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+#pragma unroll
+                for (int j = 0; j < L; ++j) buf[b][j] = buf[b + 1][j];
         }
     }
 }
@@ -263,7 +282,8 @@ __device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtD
 
 // X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
 template <int NS>
-__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N) {
+__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
+                        uint32_t* flags) {
     const size_t total = (size_t)n * slots * N;
     const int LK = NS + K;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -275,11 +295,14 @@ __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, in
         const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)NS * N + k;
         u64* dst = X + (c * 4 + slot) * (size_t)LK * N + k;
         u64 x[NS], v[NS];
+        bool bad = false;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             x[i] = src[(size_t)i * N];
             dst[(size_t)i * N] = x[i];
+            bad |= x[i] >= ext.src_q[i];
         }
+        if (bad) atomicOr(flags, BFHE_FLAG_RESIDUE);
         const bool neg = garner<NS>(x, ext, v);
         for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = ext_eval<NS, false>(v, neg, ext, j);
     }
@@ -352,7 +375,7 @@ __global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, E
 // decrypt: m = [-r Q^-1]_t with r the centred [t (c0 + c1 s)]_Q
 template <int NS>
 __global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc eQt, const u64* tmod, int nP,
-                             u64 Qinv_t, int N) {
+                             u64 Qinv_t, int N, uint32_t* flags) {
     const size_t total = (size_t)n * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -362,7 +385,9 @@ __global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const u64 qi = eQt.src_q[i];
-            const u64 vi = add_mod(V[(c * NS + i) * N + k], ct[(c * 2 * NS + i) * N + k], qi);
+            const u64 c0 = ct[(c * 2 * NS + i) * N + k];
+            if (c0 >= qi) atomicOr(flags, BFHE_FLAG_RESIDUE);
+            const u64 vi = add_mod(V[(c * NS + i) * N + k], c0, qi);
             r[i] = shoup(vi, tmod[i], tmod[nP + i], qi);
         }
         const bool neg = garner<NS>(r, eQt, v);
@@ -374,21 +399,25 @@ __global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc
 }
 
 // ---------------------------------------------------------------- encode/decode, encrypt, keygen
-__global__ void k_permute(const u64* in, u64* out, const uint32_t* brv, int n, int scatter, int N) {
+__global__ void k_permute(const u64* in, u64* out, const uint32_t* brv, int n, int scatter, int N, u64 t,
+                          uint32_t* flags) {
     const size_t total = (size_t)n * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(idx % N);
         const size_t base = idx - j;
-        if (scatter)
-            out[base + brv[j]] = in[idx];
-        else
+        if (scatter) {
+            const u64 v = in[idx];   // a slot value being encoded: must be < t
+            if (v >= t) atomicOr(flags, BFHE_FLAG_PLAINTEXT);
+            out[base + brv[j]] = v;
+        } else {
             out[idx] = in[base + brv[j]];
+        }
     }
 }
 
 __global__ void k_enc_finish(u64* ct, const u64* M, const i64* e1, const i64* e2, int n, int L, const u64* qtab,
-                             const u64* delta, int N) {
+                             const u64* delta, int N, u64 t, uint32_t* flags) {
     const size_t total = (size_t)n * L * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -397,6 +426,7 @@ __global__ void k_enc_finish(u64* ct, const u64* M, const i64* e1, const i64* e2
         const size_t c = idx / ((size_t)N * L);
         const u64 q = qtab[i];
         const u64 m = M[c * N + k];
+        if (i == 0 && m >= t) atomicOr(flags, BFHE_FLAG_PLAINTEXT);   // plaintext coefficients must be < t
         const i64 a = e1[c * N + k], b = e2[c * N + k];
         u64* c0 = ct + (c * 2 * L + i) * N + k;
         u64* c1 = c0 + (size_t)L * N;
@@ -697,7 +727,7 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
 template <int NS>
 int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const size_t work = (size_t)n * slots * ctx->N;
-    LAUNCH(k_modup<NS>, work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N);
+    LAUNCH(k_modup<NS>, work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
     return BFHE_OK;
 }
 
@@ -713,7 +743,8 @@ int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st
 template <int NS>
 int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
     const size_t work = (size_t)n * ctx->N;
-    LAUNCH(k_dec_finish<NS>, work, V, ct, M, n, ctx->ext_Qt, ctx->d_tmod, (int)ctx->nP, ctx->Qinv_t, (int)ctx->N);
+    LAUNCH(k_dec_finish<NS>, work, V, ct, M, n, ctx->ext_Qt, ctx->d_tmod, (int)ctx->nP, ctx->Qinv_t, (int)ctx->N,
+           ctx->d_flags);
     return BFHE_OK;
 }
 
@@ -775,14 +806,14 @@ int launch_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, 
 }
 
 int launch_permute(const bfhe_ctx* ctx, const u64* in, u64* out, int n, int scatter, cudaStream_t st) {
-    LAUNCH(k_permute, (size_t)n * ctx->N, in, out, ctx->d_brv, n, scatter, (int)ctx->N);
+    LAUNCH(k_permute, (size_t)n * ctx->N, in, out, ctx->d_brv, n, scatter, (int)ctx->N, ctx->t, ctx->d_flags);
     return BFHE_OK;
 }
 
 int launch_enc_finish(const bfhe_ctx* ctx, u64* ct, const u64* M, const i64* e1, const i64* e2, int n,
                       cudaStream_t st) {
     LAUNCH(k_enc_finish, (size_t)n * ctx->L * ctx->N, ct, M, e1, e2, n, (int)ctx->L, ctx->tab.q, ctx->d_delta_q,
-           (int)ctx->N);
+           (int)ctx->N, ctx->t, ctx->d_flags);
     return BFHE_OK;
 }
 

@@ -127,3 +127,43 @@ def test_tiled_paths_equal_untiled(env):
     for k in range(2):
         assert_ct_equal(prm, tiled[4][k], [want[k]], "tiled mod_to_bits bit %d" % k)
     assert np.array_equal(ctx.decrypt(tiled[0]).cpu().numpy(), (av * bv) % ctx.t)
+
+
+def test_out_of_range_inputs_are_flagged(env):
+    """Kernels raise a context flag on a plaintext value >= t or a ciphertext residue >= q_i
+    (values within the lazy ranges, so the arithmetic stays in bounds); bfhe_check reports and clears."""
+    ctx, prm, keys, bfhe = env
+    ctx.check()                                                   # nothing pending
+    good = torch.from_numpy(inputs.slots(41, 2, ctx.N, hi=ctx.t)).cuda()
+    a = ctx.encrypt(good, 41)
+    ctx.check()
+    bad = good.clone()
+    bad[1, 5] = ctx.t
+    ctx.encrypt(bad, 42)
+    with pytest.raises(bfhe.BfheError) as ei:
+        ctx.check()
+    assert ei.value.flags == 1
+    ctx.check()                                                   # cleared
+    coeffs = torch.zeros(1, ctx.N, dtype=torch.int64, device="cuda")
+    coeffs[0, 3] = ctx.t + 1
+    ctx.encrypt_poly(coeffs, 43)
+    with pytest.raises(bfhe.BfheError) as ei:
+        ctx.check()
+    assert ei.value.flags == 1
+    ctx.mul_plain(a, bad)
+    with pytest.raises(bfhe.BfheError) as ei:
+        ctx.check()
+    assert ei.value.flags == 1
+    r = a.clone()
+    r[0, 0, 0, 7] = ctx.primes[0]                                 # residue == q_0
+    ctx.mul_relin(r, a)
+    with pytest.raises(bfhe.BfheError) as ei:
+        ctx.check()
+    assert ei.value.flags == 2
+    ctx.decrypt(r)
+    with pytest.raises(bfhe.BfheError) as ei:
+        ctx.check()
+    assert ei.value.flags == 2
+    y = ctx.mul_relin(a, a)
+    ctx.check()
+    assert np.array_equal(ctx.decrypt(y).cpu().numpy(), (good.cpu().numpy() ** 2) % ctx.t)
