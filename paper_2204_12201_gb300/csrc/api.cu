@@ -66,7 +66,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         iox.in_os = iox.out_os = 4 * LK * N;
         iox.in_is = iox.out_is = LK * N;
         iox.in_ls = iox.out_ls = N;
-        RC(launch_ntt_fwd(c, iox, slots * m, (int)LK, c->mapQB(), st));
+        RC(launch_ntt_fwd(c, iox, slots * m, (int)LK, c->mapQB(), st, 1));   // tensor takes lazy words
         RC(launch_tensor(c, X, m, sq, st));
         NttIO io3;
         io3.in = X;
@@ -87,7 +87,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         iod.out_os = L * QP * N;
         iod.out_is = QP * N;
         iod.out_ls = N;
-        RC(launch_ntt_fwd(c, iod, m * (int)L, (int)QP, c->mapQP(), st));
+        RC(launch_ntt_fwd(c, iod, m * (int)L, (int)QP, c->mapQP(), st, 1));   // so does the inner product
         RC(launch_inner(c, Dg, W, m, st));
         RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st));
         RC(launch_moddown(c, W, C3, o, m, st));

@@ -243,7 +243,10 @@ inline NttIO ntt_io(const u64* in, u64* out, size_t n_limbs, size_t N) {
     io.in_ls = io.out_ls = N;
     return io;
 }
-int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st);
+// lazy_out: outputs left below 64q (only taken when every prime is below 2^50) for consumers that
+// multiply them in Montgomery form; otherwise canonical
+int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
+                   int lazy_out = 0);
 // mont != 0: the final scale is N^-1 R (undoes one Montgomery factor R^-1 of the inputs)
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
                    cudaStream_t st);

@@ -46,6 +46,12 @@ namespace {
 
 __device__ __forceinline__ int phys(int j) { return j + (j >> 4); }
 
+// padded offset of word base + (e << W_LO) relative to phys(base): no carry crosses bit 4
+// when e << W_LO is added to a pass's base (checked for every shape on the host), so the
+// offset is a compile-time constant per e
+template <int W_LO>
+__device__ __forceinline__ constexpr int poff(int e) { return (e << W_LO) + ((e << W_LO) >> 4); }
+
 struct NttArgs {
     const u64* in;
     u64* out;
@@ -55,7 +61,7 @@ struct NttArgs {
     LimbMap map;
     PrimeTab tab;
     int N, logN;
-    int mont;
+    int mont;   // inverse: inputs carry a Montgomery factor; forward: leave outputs lazy (< 64q)
 };
 
 struct LimbPtrs {
@@ -103,7 +109,7 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
 
 // TOP: this CTA is half `half` of a limb of N = 2M words and first applies the
 // outermost stage (twiddle psi^brv(1)) to the pairs (j, j + M) it reads.
-template <int LOG_M, int LOG_E, int P, bool TOP>
+template <int LOG_M, int LOG_E, int P, bool TOP, bool LAZY>
 __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* tw,
                                          u64 q, u64 mu, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
@@ -113,6 +119,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
     constexpr int LO = (HI - LOG_E + 1) > 0 ? (HI - LOG_E + 1) : 0;
     constexpr int W_LO = LO;
     const int base = (tid & ((1 << W_LO) - 1)) | ((tid >> W_LO) << (W_LO + LOG_E));
+    const int pb = phys(base);
     if (P == 0) {
         if (TOP) {
             const ulonglong2 w1 = __ldg(tw + 1);
@@ -131,25 +138,28 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
+        for (int e = 0; e < E; ++e) x[e] = sm[pb + poff<W_LO>(e)];
     }
     fwd_stages<LOG_E, W_LO, HI, LO>(x, jglob + base, tw, q);
     if constexpr (P + 1 < NPASS) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         __syncthreads();
-        fwd_pass<LOG_M, LOG_E, P + 1, TOP>(x, sm, tid, jglob, tw, q, mu, in, out, half);
+        fwd_pass<LOG_M, LOG_E, P + 1, TOP, LAZY>(x, sm, tid, jglob, tw, q, mu, in, out, half);
     } else {
-        // W_LO == 0 here: E consecutive words per thread; values < 64q -> canonical
+        // W_LO == 0 here: E consecutive words per thread; values < 64q -> canonical unless the
+        // consumer takes lazy words (Montgomery products of operands < 64q, q < 2^50)
+        if constexpr (!LAZY) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = reduce64(x[e], q, mu);
+            for (int e = 0; e < E; ++e) x[e] = reduce64(x[e], q, mu);
+        }
         ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out + base);
 #pragma unroll
         for (int e = 0; e < E / 2; ++e) o2[e] = make_ulonglong2(x[2 * e], x[2 * e + 1]);
     }
 }
 
-template <int LOG_M, int LOG_E, bool TOP>
+template <int LOG_M, int LOG_E, bool TOP, bool LAZY>
 __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 && LOG_M - LOG_E <= 8 ? 2 : 1)) k_ntt_fwd(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
@@ -159,7 +169,8 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 && LOG_M - L
     const u64 jglob = (u64)a.N + ((u64)half << LOG_M);
     const u64* in = TOP ? lp.in : lp.in + ((size_t)half << LOG_M);
     u64 x[1 << LOG_E];
-    fwd_pass<LOG_M, LOG_E, 0, TOP>(x, sm, threadIdx.x, jglob, tw, q, mu, in, lp.out + ((size_t)half << LOG_M), half);
+    fwd_pass<LOG_M, LOG_E, 0, TOP, LAZY>(x, sm, threadIdx.x, jglob, tw, q, mu, in, lp.out + ((size_t)half << LOG_M),
+                                         half);
 }
 
 // ---------------------------------------------------------------- inverse stages
@@ -204,6 +215,7 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
     constexpr int HI = (LO + LOG_E - 1) < (LOG_M - 1) ? (LO + LOG_E - 1) : (LOG_M - 1);
     constexpr int W_LO = (HI - LO + 1 == LOG_E) ? LO : (LOG_M - LOG_E);
     const int base = (tid & ((1 << W_LO) - 1)) | ((tid >> W_LO) << (W_LO + LOG_E));
+    const int pb = phys(base);
     if (P == 0) {
         // W_LO == 0: E consecutive words per thread
         const ulonglong2* i2 = reinterpret_cast<const ulonglong2*>(in + base);
@@ -215,13 +227,13 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = sm[phys(base + (e << W_LO))];
+        for (int e = 0; e < E; ++e) x[e] = sm[pb + poff<W_LO>(e)];
     }
     constexpr bool LAST = (P + 1 == NPASS);
     inv_stages<LOG_E, W_LO, LO, HI>(x, base, itw, q);
     if constexpr (!LAST) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         __syncthreads();
         inv_pass<LOG_M, LOG_E, P + 1, MODE>(x, sm, tid, itw, twist, q, in, out, half);
     } else if constexpr (MODE == 2) {
@@ -229,14 +241,14 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         // block positions through distributed shared memory, finish, twist
         cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[phys(base + (e << W_LO))] = x[e];
+        for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         cl.sync();
         const u64* peer = cl.map_shared_rank(sm, cl.block_rank() ^ 1u);
         const u64 q4 = 4 * q;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = base + (e << W_LO);
-            const u64 other = peer[phys(j)];
+            const u64 other = peer[pb + poff<W_LO>(e)];
             const u64 U = half ? other : x[e], V = half ? x[e] : other;
             const ulonglong2 wp = __ldg(itw + M + j);
             const u64 T = shoup_lazy4(V, wp.x, wp.y, q);
@@ -275,13 +287,13 @@ constexpr size_t smem_bytes() {
     return (LOG_M + LOG_E - 1) / LOG_E > 1 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : 0;
 }
 
-template <int LOG_M, int LOG_E, bool TOP>
+template <int LOG_M, int LOG_E, bool TOP, bool LAZY>
 int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
     const size_t smem = smem_bytes<LOG_M, LOG_E>();
     static bool attr = false;
     if (!attr) {
-        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E, TOP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E, TOP, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         attr = true;
     }
@@ -298,10 +310,10 @@ int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_fwd<LOG_M, LOG_E, TOP>, a));
+        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_fwd<LOG_M, LOG_E, TOP, LAZY>, a));
         BFHE_LAUNCH_CHECK("k_ntt_fwd (cluster)");
     } else {
-        k_ntt_fwd<LOG_M, LOG_E, TOP><<<dim3(blocks, 1), T, smem, st>>>(a);
+        k_ntt_fwd<LOG_M, LOG_E, TOP, LAZY><<<dim3(blocks, 1), T, smem, st>>>(a);
         BFHE_LAUNCH_CHECK("k_ntt_fwd");
     }
     return BFHE_OK;
@@ -411,23 +423,31 @@ extern "C" int bfhe_ntt_config(uint32_t logN, int inverse, uint32_t log_m, uint3
     return BFHE_OK;
 }
 
+template <int LM, int LE>
+int run_fwd_any(const NttArgs& a, int blocks, cudaStream_t st, bool top, bool lazy) {
+    if (top) return lazy ? run_fwd<LM, LE, true, true>(a, blocks, st) : run_fwd<LM, LE, true, false>(a, blocks, st);
+    return lazy ? run_fwd<LM, LE, false, true>(a, blocks, st) : run_fwd<LM, LE, false, false>(a, blocks, st);
+}
+
 #define FWD_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
-        return top ? run_fwd<LM, LE, true>(a, blocks, st) : run_fwd<LM, LE, false>(a, blocks, st);
+        return run_fwd_any<LM, LE>(a, blocks, st, top, lazy);
 #define INV_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
         return split ? run_inv<LM, LE, 2>(a, blocks, st) : run_inv<LM, LE, 1>(a, blocks, st);
 
-int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st) {
+int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
+                   int lazy_out) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
     ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
     ntt_config((int)ctx->logN, 0, &log_m, &log_e);
-    NttArgs a = make_args(ctx, io, n_limbs, map, 0);
+    NttArgs a = make_args(ctx, io, n_limbs, map, lazy_out && ctx->prime_bits <= 50 ? 1 : 0);
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
     if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
     const bool top = subs == 2;
+    const bool lazy = a.mont != 0;
     FWD_CASE(10, 3) FWD_CASE(10, 4) FWD_CASE(10, 5)
     FWD_CASE(11, 3) FWD_CASE(11, 4) FWD_CASE(11, 5)
     FWD_CASE(12, 3) FWD_CASE(12, 4) FWD_CASE(12, 5)

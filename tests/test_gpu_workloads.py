@@ -44,20 +44,25 @@ def test_every_ntt_shape_gives_the_same_transform(N):
     from paper_2204_12201_gb300 import autotune, bfhe
     logN = N.bit_length() - 1
     ctx = bfhe.Context(N=N, L=2, alpha=1)
+    ctx.keygen(2)
     x = torch.randint(0, 1 << 40, (3, 2, N), dtype=torch.int64, device="cuda")
     x %= torch.tensor(ctx.primes[:2], dtype=torch.int64, device="cuda").view(1, 2, 1)
+    cts = ctx.encrypt(torch.randint(0, 65537, (4, N), dtype=torch.int64, device="cuda"), 3)
     saved = [bfhe.ntt_config(logN, inv) for inv in (0, 1)]
-    ref_f = ref_b = None
+    ref_f = ref_m = None
     try:
         for m, e in autotune.shapes(logN):
             for inv in (0, 1):
                 bfhe.ntt_config(logN, inv, m, e)
             f = ctx.ntt(x.clone())
             b = ctx.ntt(f.clone(), inverse=True)
+            # the multiply's transforms leave lazy words for the tensor and the inner product
+            prod = ctx.mul_relin(cts[:2].contiguous(), cts[2:].contiguous())
             if ref_f is None:
-                ref_f = f
+                ref_f, ref_m = f, prod
             assert torch.equal(f, ref_f), (m, e)
             assert torch.equal(b, x), (m, e)
+            assert torch.equal(prod, ref_m), (m, e)
     finally:
         for inv, (m, e) in enumerate(saved):
             bfhe.ntt_config(logN, inv, m, e)
