@@ -27,6 +27,7 @@ LOW_T = dict(N=1024, L=2, alpha=1, t=12289)  # t - 1 = 3 * 2^12: pow with an odd
 MID = dict(N=16384, L=2, alpha=1)          # N = 16384: split-half forward NTT, whole-limb inverse
 C4 = dict(N=16384, L=8, alpha=1)           # the benchmark's parameters
 L16 = dict(N=1024, L=16, alpha=2)          # the largest limb count, two special primes (the bridge workload's)
+BIG_Q = dict(N=1024, L=2, alpha=1, prime_bits=55)   # primes above 2^50: the multiply's transforms stay canonical
 
 
 class Pair:
@@ -134,7 +135,7 @@ def test_linear_ops():
 
 @pytest.mark.parametrize("name,cfg,n", [("C1", C1, 3), ("SMALL", SMALL, 2), ("ALPHA2", ALPHA2, 2),
                                         ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2), ("MID", MID, 1),
-                                        ("L16", L16, 2)])
+                                        ("L16", L16, 2), ("BIG_Q", BIG_Q, 2)])
 def test_mul_relin(name, cfg, n):
     P = pair(name, cfg)
     prm = P.prm
@@ -243,7 +244,7 @@ def test_gate_level_matches_gates():
         assert_ct_equal(prm, wires[3 + i], [want], "level gate %s" % bridge.GATE_NAMES[g])
 
 
-@pytest.mark.parametrize("name,cfg", [("C1", C1), ("ALPHA2", ALPHA2), ("L16", L16)])
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("ALPHA2", ALPHA2), ("L16", L16), ("BIG_Q", BIG_Q)])
 def test_square_path(name, cfg):
     """mul_relin(x, x) through the squaring path equals the oracle's x * x."""
     P = pair(name, cfg)
