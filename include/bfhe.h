@@ -17,14 +17,16 @@
  *    residues canonical in [0, q_i).  A batch of n ciphertexts is n of those
  *    back to back ([n][2][L][N]).  Slot vectors are uint64 [n][N], values < t.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Calls enqueue work and return without synchronising; outputs
- *    are ready when the stream reaches that point.
+ *    stream) of the context's device, which must be the calling thread's
+ *    current CUDA device.  Calls enqueue work and return without
+ *    synchronising; outputs are ready when the stream reaches that point.
  *  - The context owns keys, tables and a scratch arena (device memory it
  *    allocates itself with cudaMalloc, grown on demand; growth synchronises
  *    the device, so reserve with bfhe_reserve before capturing a CUDA graph).
  *  - Return value: BFHE_OK (0) or a negative BFHE_E* code; no call aborts,
- *    traps or throws.  Inputs are not checked for canonical residues (cost);
- *    shapes, parameters and pointers are.
+ *    traps or throws.  Shapes, parameters and pointers are checked at the
+ *    call; value ranges (residues < q_i, plaintext values < t) are checked by
+ *    the kernels that read them and reported by bfhe_check (below).
  *  - Outputs may alias inputs only where stated.
  *  - Deterministic: the same seeds and inputs give bit-identical outputs.
  */

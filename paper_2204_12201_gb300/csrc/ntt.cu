@@ -36,6 +36,7 @@
 // for its own half.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -62,6 +63,7 @@ struct NttArgs {
     PrimeTab tab;
     int N, logN;
     int mont;   // inverse: inputs carry a Montgomery factor; forward: leave outputs lazy (< 64q)
+    int device; // host side only: the context's device (function attributes are per device)
 };
 
 struct LimbPtrs {
@@ -291,11 +293,12 @@ template <int LOG_M, int LOG_E, bool TOP, bool LAZY>
 int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
     const size_t smem = smem_bytes<LOG_M, LOG_E>();
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr{0};   // devices whose function attribute is set
+    const int dev = a.device;
+    if (!(attr.load() >> dev & 1)) {
         BFHE_CUDA(cudaFuncSetAttribute(k_ntt_fwd<LOG_M, LOG_E, TOP, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-        attr = true;
+        attr.fetch_or(1ull << dev);
     }
     if (TOP) {
         cudaLaunchConfig_t cfg = {};
@@ -324,11 +327,12 @@ int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
     // the cluster exchange needs the shared buffer even for a single pass
     const size_t smem = MODE == 2 ? (size_t)((1 << LOG_M) + ((1 << LOG_M) >> 4)) * 8 : smem_bytes<LOG_M, LOG_E>();
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr{0};   // devices whose function attribute is set
+    const int dev = a.device;
+    if (!(attr.load() >> dev & 1)) {
         BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-        attr = true;
+        attr.fetch_or(1ull << dev);
     }
     if (MODE == 2) {
         cudaLaunchConfig_t cfg = {};
@@ -369,6 +373,7 @@ NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map
     a.N = (int)ctx->N;
     a.logN = (int)ctx->logN;
     a.mont = mont;
+    a.device = ctx->device < 64 ? ctx->device : 63;
     return a;
 }
 
