@@ -27,6 +27,11 @@
  *    traps or throws.  Shapes, parameters and pointers are checked at the
  *    call; value ranges (residues < q_i, plaintext values < t) are checked by
  *    the kernels that read them and reported by bfhe_check (below).
+ *  - A context is used by one host thread at a time (its scratch arena and
+ *    operation counters are not locked); different contexts are independent.
+ *    Calls on one context with different streams are ordered only by the
+ *    caller: the arena is shared, so put one context's calls on one stream
+ *    or synchronise between streams.
  *  - Outputs may alias inputs only where stated.
  *  - Deterministic: the same seeds and inputs give bit-identical outputs.
  */
