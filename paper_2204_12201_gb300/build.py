@@ -69,5 +69,22 @@ def build(verbose=False, force=False):
     return lib
 
 
+def build_demo():
+    """Compile examples/abi_demo.c against the library (plain C through the ABI); returns its path."""
+    lib = build()
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler")
+    cuda = os.path.dirname(os.path.dirname(_nvcc()))
+    out = os.path.join(LIBDIR, "abi_demo")
+    cmd = [cc, "-O2", "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+           os.path.join(PKG, "examples", "abi_demo.c"), "-o", out, "-L", LIBDIR, "-lbfhe",
+           "-L", os.path.join(cuda, "lib64"), "-lcudart", "-Wl,-rpath," + LIBDIR]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("demo build failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+    return out, lib
+
+
 if __name__ == "__main__":
     print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
