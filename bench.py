@@ -240,6 +240,11 @@ def extras(torch, bfhe, circuits, ctx16):
         return e0.elapsed_time(e1) / reps
 
     ms_b = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
+    # the same batched multiply with the guarded fast base extension (same words, other speed)
+    ctx16.set_fast_extension(True)
+    ms_f = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
+    ctx16.set_fast_extension(False)
+    out["mul_relin_batched_fast_extension_per_s"] = B / ms_f * 1e3
     ms_p = timed(lambda: [ctx16.mul_relin(a[i:i + 1], b[i:i + 1], out=o[i:i + 1]) for i in range(B)], 3)
     out["mul_relin_batched_per_s"] = B / ms_b * 1e3
     out["mul_relin_per_op_per_s"] = B / ms_p * 1e3

@@ -72,6 +72,7 @@ def load():
         "bfhe_launch_count": (ctypes.c_uint64, []),
         "bfhe_set_scratch_budget": (I, [S]),
         "bfhe_check": (I, [P, P, P]),
+        "bfhe_set_fast_extension": (I, [P, I]),
         "bfhe_scratch_budget": (S, []),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
@@ -155,6 +156,10 @@ class Context:
             err = BfheError("out-of-range input (flags %d): %s" % (f.value, self.lib.bfhe_last_error().decode()))
             err.flags = f.value
             raise err
+
+    def set_fast_extension(self, on):
+        """Guarded fast base extension in the multiply (same results, different speed)."""
+        _check(self.lib.bfhe_set_fast_extension(self.h, int(bool(on))))
 
     def reserve(self, n):
         _check(self.lib.bfhe_reserve(self.h, n))

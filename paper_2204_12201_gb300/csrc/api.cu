@@ -181,6 +181,14 @@ extern "C" int bfhe_check(bfhe_ctx* c, void* stream, uint32_t* flags_out) {
     return BFHE_OK;
 }
 
+extern "C" int bfhe_set_fast_extension(bfhe_ctx* c, int on) {
+    CHECK_CTX(c);
+    if (on && !(c->ext_QB.fast_ok && c->ext_BQ.fast_ok))
+        return set_error(BFHE_EINVAL, "the fast extension needs every modulus below 2^50");
+    c->fast_ext = on != 0;
+    return BFHE_OK;
+}
+
 extern "C" int bfhe_set_scratch_budget(size_t bytes) {
     // one multiply at the largest parameters needs far less than 1 MiB x 64; below 1 MiB nothing fits
     if (bytes < ((size_t)1 << 20)) return set_error(BFHE_EINVAL, "scratch budget below 1 MiB");

@@ -110,6 +110,17 @@ struct ExtDesc {
     const u64* radix;    // [n_dst][n_src]: [s_i]_{T_j} (Shoup pair)
     const u64* radix_s;
     const u64* smod;     // [n_dst]: [S]_{T_j}
+    // guarded fast path (all moduli < 2^50): x = sum_i y_i (S/s_i) - v S with y_i = [x_i (S/s_i)^-1]_{s_i}
+    // and v = round(sum_i y_i / s_i) from a 64.64 fixed-point sum, unless that sum lies within
+    // 2 n_src + 2 units of 1/2 (then the exact mixed-radix path decides)
+    const u64* qhinv;    // [n_src] [(S/s_i)^-1]_{s_i} (Shoup pair)
+    const u64* qhinv_s;
+    const u64* g_hi;     // [n_src] floor(2^128 / s_i) >> 64
+    const u64* g_lo;     // [n_src] floor(2^128 / s_i) mod 2^64
+    const uint32_t* c26; // [n_dst][n_src][2] 26-bit limbs (low, high) of [(S/s_i) 2^64]_{T_j}
+    const u64* dst_qinv; // [n_dst] -T_j^-1 mod 2^64
+    const u64* vS;       // [n_dst][n_src + 1] [v S]_{T_j}
+    int fast_ok;         // all moduli < 2^50: the fast path's tables are valid
 };
 
 // Device-side prime tables of a context, by prime index
@@ -169,6 +180,7 @@ struct bfhe_ctx {
     size_t reserve_n = 0;
 
     uint64_t counts[4] = {0, 0, 0, 0};
+    bool fast_ext = false;       // guarded fast base extension in the multiply (bfhe_set_fast_extension)
 
     // launch timing (measurement only): pending (class, start, stop) event triples
     struct ProfRec {

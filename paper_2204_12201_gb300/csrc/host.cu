@@ -134,8 +134,9 @@ struct Arena {
 };
 
 struct ExtOffsets {
-    int n, m;
+    int n, m, fast_ok;
     size_t src_q, ginv, ginv_s, hdig, dst_q, dst_mu, radix, radix_s, smod;
+    size_t qhinv, qhinv_s, g_hi, g_lo, c26, dst_qinv, vS;
 };
 
 ExtOffsets build_ext(Arena& ar, const std::vector<u64>& src, const std::vector<u64>& dst) {
@@ -161,9 +162,52 @@ ExtOffsets build_ext(Arena& ar, const std::vector<u64>& src, const std::vector<u
         smod[j] = prod;
         mu[j] = (u64)(((u128)1 << 64) / dst[j]);
     }
+    // guarded fast path tables
+    bool fast_ok = true;
+    for (u64 v : src) fast_ok = fast_ok && v < ((u64)1 << 50);
+    for (u64 v : dst) fast_ok = fast_ok && v < ((u64)1 << 50);
+    std::vector<u64> qhinv(n), qhinv_s(n), g_hi(n), g_lo(n), dqinv(m), vS((size_t)m * (n + 1));
+    std::vector<u64> c26w(((size_t)m * n * 2 + 1) / 2 + 1, 0);   // uint32 pairs packed in u64 words
+    uint32_t* c26 = reinterpret_cast<uint32_t*>(c26w.data());
+    for (int i = 0; i < n; ++i) {
+        u64 qh = 1;   // (S / s_i) mod s_i
+        for (int k = 0; k < n; ++k)
+            if (k != i) qh = mulmod(qh, src[k] % src[i], src[i]);
+        qhinv[i] = invmod(qh, src[i]);
+        qhinv_s[i] = shoup_of(qhinv[i], src[i]);
+        const u128 g = (~(u128)0) / src[i];   // floor(2^128 / s) for s not a power of two
+        g_hi[i] = (u64)(g >> 64);
+        g_lo[i] = (u64)g;
+    }
+    for (int j = 0; j < m; ++j) {
+        const u64 T = dst[j];
+        u64 x = T;   // Newton: T * x = 1 mod 2^64
+        for (int it = 0; it < 6; ++it) x *= 2 - T * x;
+        dqinv[j] = (u64)0 - x;
+        const u64 R = (u64)(((u128)1 << 64) % T);
+        u64 S_T = 1 % T;
+        for (int k = 0; k < n; ++k) S_T = mulmod(S_T, src[k] % T, T);
+        for (int v = 0; v <= n; ++v) vS[(size_t)j * (n + 1) + v] = mulmod((u64)v % T, S_T, T);
+        for (int i = 0; i < n; ++i) {
+            u64 qh = 1 % T;   // (S / s_i) mod T
+            for (int k = 0; k < n; ++k)
+                if (k != i) qh = mulmod(qh, src[k] % T, T);
+            const u64 cv = mulmod(qh, R, T);
+            c26[((size_t)j * n + i) * 2 + 0] = (uint32_t)(cv & 0x3FFFFFFull);
+            c26[((size_t)j * n + i) * 2 + 1] = (uint32_t)(cv >> 26);
+        }
+    }
     ExtOffsets o;
     o.n = n;
     o.m = m;
+    o.fast_ok = fast_ok ? 1 : 0;
+    o.qhinv = ar.add(qhinv);
+    o.qhinv_s = ar.add(qhinv_s);
+    o.g_hi = ar.add(g_hi);
+    o.g_lo = ar.add(g_lo);
+    o.c26 = ar.add(c26w);
+    o.dst_qinv = ar.add(dqinv);
+    o.vS = ar.add(vS);
     o.src_q = ar.add(src);
     o.ginv = ar.add(ginv);
     o.ginv_s = ar.add(ginv_s);
@@ -189,6 +233,14 @@ ExtDesc ext_ptrs(const u64* base, const ExtOffsets& o) {
     d.radix = base + o.radix;
     d.radix_s = base + o.radix_s;
     d.smod = base + o.smod;
+    d.qhinv = base + o.qhinv;
+    d.qhinv_s = base + o.qhinv_s;
+    d.g_hi = base + o.g_hi;
+    d.g_lo = base + o.g_lo;
+    d.c26 = reinterpret_cast<const uint32_t*>(base + o.c26);
+    d.dst_qinv = base + o.dst_qinv;
+    d.vS = base + o.vS;
+    d.fast_ok = o.fast_ok;
     return d;
 }
 

@@ -280,8 +280,63 @@ __device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtD
     return acc;
 }
 
-// X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
+// Guarded fast exact extension (all moduli below 2^50), first half: y_i = [x_i (S/s_i)^-1]_{s_i} split
+// into 26-bit limbs, and v = round(sum_i y_i / s_i) from the 64.64 fixed-point sum of
+// floor(y_i floor(2^128/s_i) / 2^64) (each term at most 2 units below y_i 2^64 / s_i).  Returns false
+// when the fraction lies within 2n + 2 units of 1/2: then the caller takes the exact mixed-radix path.
 template <int NS>
+__device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, uint32_t (&y0)[NS],
+                                          uint32_t (&y1)[NS], int& v) {
+    u64 lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const u64 s = d.src_q[i];
+        const u64 y = shoup(x[i], d.qhinv[i], d.qhinv_s[i], s);
+        y0[i] = (uint32_t)(y & 0x3FFFFFFull);
+        y1[i] = (uint32_t)(y >> 26);
+        const u64 term = y * d.g_hi[i] + __umul64hi(y, d.g_lo[i]);
+        lo += term;
+        hi += lo < term ? 1ull : 0ull;
+    }
+    const u64 half = 1ull << 63;
+    if (lo > half) {
+        v = (int)hi + 1;
+        return true;
+    }
+    if (lo + (u64)(2 * NS + 2) <= half) {
+        v = (int)hi;
+        return true;
+    }
+    return false;
+}
+
+// second half: sum_i y_i [(S/s_i) 2^64]_{T_j} with the 26-bit limb products accumulated in four 64-bit
+// words (no carries below 2^13 sources), one Montgomery reduction, minus [v S]_{T_j}; canonical result
+template <int NS>
+__device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_t (&y1)[NS], int v, const ExtDesc& d,
+                                         int j) {
+    const uint32_t* c = d.c26 + (size_t)j * NS * 2;
+    u64 p00 = 0, p01 = 0, p10 = 0, p11 = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const uint32_t c0 = c[2 * i], c1 = c[2 * i + 1];
+        p00 += (u64)y0[i] * c0;
+        p01 += (u64)y0[i] * c1;
+        p10 += (u64)y1[i] * c0;
+        p11 += (u64)y1[i] * c1;
+    }
+    const u64 mid = p01 + p10;                       // weight 2^26
+    u64 lo = p00 + (mid << 26);
+    u64 hi = (mid >> 38) + (lo < p00 ? 1ull : 0ull);
+    const u64 top = p11 << 52;                       // weight 2^52
+    lo += top;
+    hi += (p11 >> 12) + (lo < top ? 1ull : 0ull);
+    const u64 T = d.dst_q[j];
+    return sub_mod(redc(hi, lo, T, d.dst_qinv[j]), d.vS[(size_t)j * (NS + 1) + v], T);
+}
+
+// X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
+template <int NS, bool FAST>
 __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
                         uint32_t* flags) {
     const size_t total = (size_t)n * slots * N;
@@ -294,7 +349,7 @@ __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, in
         const int slot = (int)(pp % slots);
         const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)NS * N + k;
         u64* dst = X + (c * 4 + slot) * (size_t)LK * N + k;
-        u64 x[NS], v[NS];
+        u64 x[NS];
         bool bad = false;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
@@ -303,13 +358,22 @@ __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, in
             bad |= x[i] >= ext.src_q[i];
         }
         if (bad) atomicOr(flags, BFHE_FLAG_RESIDUE);
+        if constexpr (FAST) {
+            uint32_t y0[NS], y1[NS];
+            int vv = 0;
+            if (fast_prep<NS>(x, ext, y0, y1, vv)) {
+                for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = fast_eval<NS>(y0, y1, vv, ext, j);
+                continue;
+            }
+        }
+        u64 v[NS];
         const bool neg = garner<NS>(x, ext, v);
         for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = ext_eval<NS, false>(v, neg, ext, j);
     }
 }
 
 // scale-and-round of the tensor (X slots 0..2, Q u B limbs) into C3 [n][3][L][N]
-template <int NS, int KS>
+template <int NS, int KS, bool FAST>
 __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* tmod, int nP,
                         const u64* Qinv_b, const u64* bq, int N) {
     const size_t total = (size_t)n * 3 * N;
@@ -321,24 +385,46 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
         const size_t c = cp / 3;
         const int comp = (int)(cp % 3);
         const u64* d = X + (c * 4 + comp) * (size_t)LK * N + k;
-        u64 r[NS], v[NS];
+        u64 r[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const u64 qi = eQB.src_q[i];
             r[i] = shoup_lazy(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);   // [t d]_{q_i}, < 2 q_i
         }
-        const bool neg = garner<NS>(r, eQB, v);
-        u64 y[KS], w[KS];
+        // r -> B (centred), then y = (t d - r) / Q in B
+        u64 y[KS];
+        {
+            uint32_t r0[NS], r1[NS];
+            int vv = 0;
+            bool fast = false;
+            if constexpr (FAST) fast = fast_prep<NS>(r, eQB, r0, r1, vv);
+            u64 v[NS];
+            bool neg = false;
+            if (!fast) neg = garner<NS>(r, eQB, v);
 #pragma unroll
-        for (int j = 0; j < KS; ++j) {
-            const u64 bj = bq[j];
-            const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
-            const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);   // < 2 b_j
-            const u64 rb = ext_eval<NS, false>(v, neg, eQB, j);
-            y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
+            for (int j = 0; j < KS; ++j) {
+                const u64 bj = bq[j];
+                const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
+                const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);   // < 2 b_j
+                u64 rb;
+                if constexpr (FAST) rb = fast ? fast_eval<NS>(r0, r1, vv, eQB, j) : ext_eval<NS, false>(v, neg, eQB, j);
+                else rb = ext_eval<NS, false>(v, neg, eQB, j);
+                y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
+            }
         }
-        const bool negy = garner<KS>(y, eBQ, w);
+        // y -> Q (centred)
         u64* o = C3 + cp * (size_t)NS * N + k;
+        if constexpr (FAST) {
+            uint32_t y0[KS], y1[KS];
+            int vy = 0;
+            if (fast_prep<KS>(y, eBQ, y0, y1, vy)) {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS>(y0, y1, vy, eBQ, i);
+                continue;
+            }
+        }
+        u64 w[KS];
+        const bool negy = garner<KS>(y, eBQ, w);
 #pragma unroll
         for (int i = 0; i < NS; ++i) o[(size_t)i * N] = ext_eval<KS, false>(w, negy, eBQ, i);
     }
@@ -727,7 +813,10 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
 template <int NS>
 int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const size_t work = (size_t)n * slots * ctx->N;
-    LAUNCH(k_modup<NS>, work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
+    if (ctx->fast_ext && ctx->ext_QB.fast_ok)
+        LAUNCH((k_modup<NS, true>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
+    else
+        LAUNCH((k_modup<NS, false>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
     return BFHE_OK;
 }
 
@@ -735,8 +824,12 @@ template <int NS>
 int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
     const size_t work = (size_t)n * 3 * ctx->N;
     const u64* bq = ctx->tab.q + ctx->L + ctx->alpha;
-    LAUNCH((k_scale<NS, NS + 1>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
-           ctx->d_Qinv_b, bq, (int)ctx->N);
+    if (ctx->fast_ext && ctx->ext_QB.fast_ok && ctx->ext_BQ.fast_ok)
+        LAUNCH((k_scale<NS, NS + 1, true>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
+               ctx->d_Qinv_b, bq, (int)ctx->N);
+    else
+        LAUNCH((k_scale<NS, NS + 1, false>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
+               ctx->d_Qinv_b, bq, (int)ctx->N);
     return BFHE_OK;
 }
 

@@ -317,3 +317,36 @@ def test_mod_to_sint(sign, mode):
     for k in range(s):
         assert_ct_equal(prm, got[k], [want[k]], "mod_to_sint bit %d" % k)
     assert P.ctx.op_counts()[:3] == ev.counts()
+
+
+# ------------------------------------------------------------ guarded fast base extension
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("ALPHA2", ALPHA2), ("L16", L16), ("MID", MID)])
+def test_fast_extension_gives_the_same_ciphertexts(name, cfg):
+    """With the guarded fast extension on, multiplies (general and squaring) equal the oracle word for
+    word, including coefficients at the centring boundary, where the guard sends the extension
+    to the exact mixed-radix path."""
+    P = pair(name, cfg)
+    prm = P.prm
+    Q = prm.Q
+    y = inputs.slots(61, 4, prm.N, hi=prm.t)
+    a = P.enc(y[0], 71, 0)
+    b = P.enc(y[1], 71, 1)
+    special = [(Q - 1) // 2, (Q + 1) // 2, 0, Q - 1, 1]
+    e = ([special[k % 5] if k < 10 else x for k, x in enumerate(a[0])], a[1])
+    want = [bfv.mul_relin(prm, P.keys, a, b), bfv.mul_relin(prm, P.keys, e, b), bfv.mul_relin(prm, P.keys, a, a)]
+    P.ctx.set_fast_extension(True)
+    try:
+        got = P.ctx.mul_relin(cts_to_device(prm, [a, e]), cts_to_device(prm, [b, b]))
+        da = cts_to_device(prm, [a])
+        sq = P.ctx.mul_relin(da, da)
+    finally:
+        P.ctx.set_fast_extension(False)
+    assert_ct_equal(prm, got, want[:2], "fast extension %s" % name)
+    assert_ct_equal(prm, sq, want[2:], "fast extension square %s" % name)
+
+
+def test_fast_extension_needs_small_moduli():
+    from paper_2204_12201_gb300 import bfhe
+    P = pair("BIG_Q", BIG_Q)
+    with pytest.raises(bfhe.BfheError):
+        P.ctx.set_fast_extension(True)
