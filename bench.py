@@ -240,11 +240,13 @@ def extras(torch, bfhe, circuits, ctx16):
         return e0.elapsed_time(e1) / reps
 
     ms_b = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
-    # the same batched multiply with the guarded fast base extension (same words, other speed)
-    ctx16.set_fast_extension(True)
-    ms_f = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
-    ctx16.set_fast_extension(False)
-    out["mul_relin_batched_fast_extension_per_s"] = B / ms_f * 1e3
+    # the same batched multiply with each base extension forced (same words, other speed)
+    default = ctx16.fast_extension
+    for fast in (False, True):
+        ctx16.set_fast_extension(fast)
+        ms_x = timed(lambda: ctx16.mul_relin(a, b, out=o), 5)
+        out["mul_relin_batched_%s_extension_per_s" % ("fast" if fast else "exact")] = B / ms_x * 1e3
+    ctx16.set_fast_extension(default)
     ms_p = timed(lambda: [ctx16.mul_relin(a[i:i + 1], b[i:i + 1], out=o[i:i + 1]) for i in range(B)], 3)
     out["mul_relin_batched_per_s"] = B / ms_b * 1e3
     out["mul_relin_per_op_per_s"] = B / ms_p * 1e3
@@ -450,6 +452,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {**base_config(), "mul_relin_per_step": n_mul // args.steps,
+                           "base_extension": "guarded fast, exact fallback" if ctx.fast_extension else "exact Garner",
                            "parallelism": "replicas" if world > 1 else "single",
                            "ntt_shapes": {k: v["shape"] for k, v in shapes.items()},
                            "l2": "no flush: per-step working set > 10 GB >> 129 MB L2"},

@@ -97,7 +97,7 @@ int bfhe_check(bfhe_ctx* ctx, void* stream, uint32_t* flags_out);
  * growth, hence device synchronisation, inside later calls). */
 int bfhe_reserve(bfhe_ctx* ctx, size_t n);
 
-/* Guarded fast base extension inside the multiply (off by default).  The
+/* Guarded fast base extension inside the multiply.  The
  * exact extensions of the lift (Q -> B) and of the scale-and-round (Q -> B,
  * B -> Q) normally run Garner's mixed-radix digits.  With this on they first
  * try y_i = [x_i (S/s_i)^-1]_{s_i}, x = sum_i y_i (S/s_i) - v S with v =
@@ -105,9 +105,13 @@ int bfhe_reserve(bfhe_ctx* ctx, size_t n);
  * mixed-radix path when that sum is within 2n + 2 units of 1/2, where the
  * fixed-point rounding could pick the wrong v.  Results are identical
  * either way (bit for bit); only the speed differs.  Needs every modulus
- * below 2^50 (BFHE_EINVAL otherwise).  The paper has no counterpart: SEAL,
- * which it runs on, uses approximate fast conversions of this family. */
+ * below 2^50 (BFHE_EINVAL otherwise).  Default: on from 8 data primes up
+ * (where it measured faster on GB300), off below.  bfhe_fast_extension
+ * returns the current setting (1 or 0; BFHE_EINVAL for a NULL context).  The
+ * paper has no counterpart: SEAL, which it runs on, uses approximate fast
+ * conversions of this family. */
 int bfhe_set_fast_extension(bfhe_ctx* ctx, int on);
+int bfhe_fast_extension(const bfhe_ctx* ctx);
 
 /* Process-wide device-memory budget for one call's scratch (default 16 GiB).
  * Calls whose batch needs more are tiled: the multiplies run in chunks that

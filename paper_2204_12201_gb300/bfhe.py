@@ -73,6 +73,7 @@ def load():
         "bfhe_set_scratch_budget": (I, [S]),
         "bfhe_check": (I, [P, P, P]),
         "bfhe_set_fast_extension": (I, [P, I]),
+        "bfhe_fast_extension": (I, [P]),
         "bfhe_scratch_budget": (S, []),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
@@ -160,6 +161,13 @@ class Context:
     def set_fast_extension(self, on):
         """Guarded fast base extension in the multiply (same results, different speed)."""
         _check(self.lib.bfhe_set_fast_extension(self.h, int(bool(on))))
+
+    @property
+    def fast_extension(self):
+        rc = self.lib.bfhe_fast_extension(self.h)
+        if rc < 0:
+            _check(rc)
+        return bool(rc)
 
     def reserve(self, n):
         _check(self.lib.bfhe_reserve(self.h, n))

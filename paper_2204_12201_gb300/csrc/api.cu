@@ -189,6 +189,11 @@ extern "C" int bfhe_set_fast_extension(bfhe_ctx* c, int on) {
     return BFHE_OK;
 }
 
+extern "C" int bfhe_fast_extension(const bfhe_ctx* c) {
+    if (!c) return set_error(BFHE_EINVAL, "null context");
+    return c->fast_ext ? 1 : 0;
+}
+
 extern "C" int bfhe_set_scratch_budget(size_t bytes) {
     // one multiply at the largest parameters needs far less than 1 MiB x 64; below 1 MiB nothing fits
     if (bytes < ((size_t)1 << 20)) return set_error(BFHE_EINVAL, "scratch budget below 1 MiB");

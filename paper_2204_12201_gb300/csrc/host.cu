@@ -588,6 +588,8 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->ext_BQ = ext_ptrs(base, eBQ);
     c->ext_PQ = ext_ptrs(base, ePQ);
     c->ext_Qt = ext_ptrs(base, eQt);
+    // the guarded fast extension measures faster from 8 data primes up (slower at 2)
+    c->fast_ext = c->L >= 8 && c->ext_QB.fast_ok && c->ext_BQ.fast_ok;
     c->d_tmod = base + o_tmod;
     c->d_delta_q = base + o_delta;
     c->d_Qinv_b = base + o_Qinvb;

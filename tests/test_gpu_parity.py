@@ -334,19 +334,23 @@ def test_fast_extension_gives_the_same_ciphertexts(name, cfg):
     special = [(Q - 1) // 2, (Q + 1) // 2, 0, Q - 1, 1]
     e = ([special[k % 5] if k < 10 else x for k, x in enumerate(a[0])], a[1])
     want = [bfv.mul_relin(prm, P.keys, a, b), bfv.mul_relin(prm, P.keys, e, b), bfv.mul_relin(prm, P.keys, a, a)]
-    P.ctx.set_fast_extension(True)
+    default = P.ctx.fast_extension
+    assert default == (prm.L >= 8)
     try:
-        got = P.ctx.mul_relin(cts_to_device(prm, [a, e]), cts_to_device(prm, [b, b]))
-        da = cts_to_device(prm, [a])
-        sq = P.ctx.mul_relin(da, da)
+        for fast in (False, True):
+            P.ctx.set_fast_extension(fast)
+            got = P.ctx.mul_relin(cts_to_device(prm, [a, e]), cts_to_device(prm, [b, b]))
+            da = cts_to_device(prm, [a])
+            sq = P.ctx.mul_relin(da, da)
+            assert_ct_equal(prm, got, want[:2], "extension (fast=%s) %s" % (fast, name))
+            assert_ct_equal(prm, sq, want[2:], "extension (fast=%s) square %s" % (fast, name))
     finally:
-        P.ctx.set_fast_extension(False)
-    assert_ct_equal(prm, got, want[:2], "fast extension %s" % name)
-    assert_ct_equal(prm, sq, want[2:], "fast extension square %s" % name)
+        P.ctx.set_fast_extension(default)
 
 
 def test_fast_extension_needs_small_moduli():
     from paper_2204_12201_gb300 import bfhe
     P = pair("BIG_Q", BIG_Q)
+    assert not P.ctx.fast_extension
     with pytest.raises(bfhe.BfheError):
         P.ctx.set_fast_extension(True)
