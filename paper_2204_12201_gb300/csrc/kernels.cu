@@ -315,11 +315,12 @@ __device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, 
 template <int NS>
 __device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_t (&y1)[NS], int v, const ExtDesc& d,
                                          int j) {
-    const uint32_t* c = d.c26 + (size_t)j * NS * 2;
+    const uint2* c = reinterpret_cast<const uint2*>(d.c26) + (size_t)j * NS;   // (low, high) limb pairs, 8-byte aligned
     u64 p00 = 0, p01 = 0, p10 = 0, p11 = 0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        const uint32_t c0 = c[2 * i], c1 = c[2 * i + 1];
+        const uint2 cc = __ldg(c + i);
+        const uint32_t c0 = cc.x, c1 = cc.y;
         p00 += (u64)y0[i] * c0;
         p01 += (u64)y0[i] * c1;
         p10 += (u64)y1[i] * c0;
