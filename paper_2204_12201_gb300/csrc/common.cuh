@@ -45,17 +45,6 @@ __host__ __device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 ws, u64 q) 
     return a * w - mulhi64(a, ws) * q;
 }
 
-// a * w mod q in [0, 3q) for a < 2^64: the quotient estimate drops the low 32x32
-// partial product of a * ws, so it is floor(a ws / 2^64) or one less (three wide
-// 32x32 products instead of four).
-__host__ __device__ __forceinline__ u64 shoup_lazy3(u64 a, u64 w, u64 ws, u64 q) {
-    const u64 a1 = a >> 32, a0 = a & 0xffffffffull, w1 = ws >> 32, w0 = ws & 0xffffffffull;
-    const u64 p10 = a1 * w0, p01 = a0 * w1;
-    const u64 mid = p10 + p01;
-    const u64 hi = a1 * w1 + (mid >> 32) + (mid < p10 ? (1ull << 32) : 0ull);
-    return a * w - hi * q;
-}
-
 // a * w mod q in [0, 4q) for a < 2^64: the quotient estimate keeps a1 w1 and the high
 // halves of the two cross products a1 w0, a0 w1 (their low halves and a0 w0 together are
 // below 3 2^64), so it is floor(a ws / 2^64) minus 0, 1 or 2, and Shoup's own estimate
