@@ -75,7 +75,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         io3.in_os = io3.out_os = 4 * LK * N;
         io3.in_is = io3.out_is = LK * N;
         io3.in_ls = io3.out_ls = N;
-        RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st));
+        RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st, 1));   // scale takes words < 2q
         RC(launch_scale(c, X, C3, m, st));
         NttIO iod;   // digit j of c2 (limb j of C3 slot 2), reduced into every prime of Q u P
         iod.in = C3 + 2 * L * N;
@@ -89,7 +89,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         iod.out_ls = N;
         RC(launch_ntt_fwd(c, iod, m * (int)L, (int)QP, c->mapQP(), st, 1));   // so does the inner product
         RC(launch_inner(c, Dg, W, m, st));
-        RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st));
+        RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st, 1));   // so does mod-down
         RC(launch_moddown(c, W, C3, o, m, st));
     }
     return BFHE_OK;

@@ -249,7 +249,9 @@ inline NttIO ntt_io(const u64* in, u64* out, size_t n_limbs, size_t N) {
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
                    int lazy_out = 0);
 // mont != 0: the final scale is N^-1 R (undoes one Montgomery factor R^-1 of the inputs)
+// lazy_out: outputs below 2q (the twist product without its final subtraction) for consumers that
+// take lazy words (scale-and-round, mod-down); otherwise canonical
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
-                   cudaStream_t st);
+                   cudaStream_t st, int lazy_out = 0);
 int ntt_config(int logN, int inverse, int* log_m, int* log_e);
 void ntt_set_log_e(int log_e);   // tuning override (0 = default)

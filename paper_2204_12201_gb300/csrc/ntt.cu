@@ -62,7 +62,8 @@ struct NttArgs {
     LimbMap map;
     PrimeTab tab;
     int N, logN;
-    int mont;   // inverse: inputs carry a Montgomery factor; forward: leave outputs lazy (< 64q)
+    int mont;   // inverse: inputs carry a Montgomery factor
+    int lazy;   // host side only: forward outputs < 64q / inverse outputs < 2q (selects the template)
     int device; // host side only: the context's device (function attributes are per device)
 };
 
@@ -207,7 +208,7 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const
 
 // MODE 1: the block is the whole limb; MODE 2: half `half` of a limb of N = 2M words,
 // whose outermost stage pairs with the partner CTA of the cluster.
-template <int LOG_M, int LOG_E, int P, int MODE>
+template <int LOG_M, int LOG_E, int P, int MODE, bool LAZY>
 __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, const ulonglong2* itw,
                                          const ulonglong2* twist, u64 q, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         __syncthreads();
-        inv_pass<LOG_M, LOG_E, P + 1, MODE>(x, sm, tid, itw, twist, q, in, out, half);
+        inv_pass<LOG_M, LOG_E, P + 1, MODE, LAZY>(x, sm, tid, itw, twist, q, in, out, half);
     } else if constexpr (MODE == 2) {
         // outermost stage across the halves: publish, read the partner's words at the same
         // block positions through distributed shared memory, finish, twist
@@ -256,7 +257,7 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
             const u64 T = shoup_lazy4(V, wp.x, wp.y, q);
             const u64 y = half ? U + q4 - T : U + T;
             const ulonglong2 tw = __ldg(twist + j + half * M);
-            out[j] = shoup(y, tw.x, tw.y, q);
+            out[j] = LAZY ? shoup_lazy(y, tw.x, tw.y, q) : shoup(y, tw.x, tw.y, q);
         }
         cl.sync();   // the partner has finished reading this CTA's shared memory
     } else {
@@ -264,12 +265,12 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         for (int e = 0; e < E; ++e) {
             const int j = base + (e << W_LO);
             const ulonglong2 tw = __ldg(twist + j);
-            out[j] = shoup(x[e], tw.x, tw.y, q);
+            out[j] = LAZY ? shoup_lazy(x[e], tw.x, tw.y, q) : shoup(x[e], tw.x, tw.y, q);
         }
     }
 }
 
-template <int LOG_M, int LOG_E, int MODE>
+template <int LOG_M, int LOG_E, int MODE, bool LAZY>
 __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14 && LOG_M - LOG_E <= 8 ? 2 : 1)) k_ntt_inv(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14
     const ulonglong2* itw = reinterpret_cast<const ulonglong2*>(a.tab.itw) + (size_t)lp.p * a.N;
     const ulonglong2* twist = reinterpret_cast<const ulonglong2*>(a.tab.twist) + ((size_t)lp.p * 2 + (a.mont ? 1 : 0)) * a.N;
     u64 x[1 << LOG_E];
-    inv_pass<LOG_M, LOG_E, 0, MODE>(x, sm, threadIdx.x, itw, twist, q, lp.in + ((size_t)half << LOG_M),
+    inv_pass<LOG_M, LOG_E, 0, MODE, LAZY>(x, sm, threadIdx.x, itw, twist, q, lp.in + ((size_t)half << LOG_M),
                                     lp.out + ((size_t)half << LOG_M), half);
 }
 
@@ -322,7 +323,7 @@ int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
     return BFHE_OK;
 }
 
-template <int LOG_M, int LOG_E, int MODE>
+template <int LOG_M, int LOG_E, int MODE, bool LAZY>
 int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
     // the cluster exchange needs the shared buffer even for a single pass
@@ -330,7 +331,7 @@ int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     static std::atomic<uint64_t> attr{0};   // devices whose function attribute is set
     const int dev = a.device;
     if (!(attr.load() >> dev & 1)) {
-        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         attr.fetch_or(1ull << dev);
     }
@@ -347,16 +348,16 @@ int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_inv<LOG_M, LOG_E, MODE>, a));
+        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_inv<LOG_M, LOG_E, MODE, LAZY>, a));
         BFHE_LAUNCH_CHECK("k_ntt_inv (cluster)");
     } else {
-        k_ntt_inv<LOG_M, LOG_E, MODE><<<dim3(blocks, 1), T, smem, st>>>(a);
+        k_ntt_inv<LOG_M, LOG_E, MODE, LAZY><<<dim3(blocks, 1), T, smem, st>>>(a);
         BFHE_LAUNCH_CHECK("k_ntt_inv");
     }
     return BFHE_OK;
 }
 
-NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map, int mont) {
+NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map, int mont, int lazy) {
     NttArgs a;
     a.in = io.in;
     a.out = io.out;
@@ -373,6 +374,7 @@ NttArgs make_args(const bfhe_ctx* ctx, const NttIO& io, int n_limbs, LimbMap map
     a.N = (int)ctx->N;
     a.logN = (int)ctx->logN;
     a.mont = mont;
+    a.lazy = lazy;
     a.device = ctx->device < 64 ? ctx->device : 63;
     return a;
 }
@@ -437,9 +439,15 @@ int run_fwd_any(const NttArgs& a, int blocks, cudaStream_t st, bool top, bool la
 #define FWD_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
         return run_fwd_any<LM, LE>(a, blocks, st, top, lazy);
+template <int LM, int LE>
+int run_inv_any(const NttArgs& a, int blocks, cudaStream_t st, bool split, bool lazy) {
+    if (split) return lazy ? run_inv<LM, LE, 2, true>(a, blocks, st) : run_inv<LM, LE, 2, false>(a, blocks, st);
+    return lazy ? run_inv<LM, LE, 1, true>(a, blocks, st) : run_inv<LM, LE, 1, false>(a, blocks, st);
+}
+
 #define INV_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
-        return split ? run_inv<LM, LE, 2>(a, blocks, st) : run_inv<LM, LE, 1>(a, blocks, st);
+        return run_inv_any<LM, LE>(a, blocks, st, split, lazy);
 
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
                    int lazy_out) {
@@ -447,12 +455,12 @@ int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
     ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
     ntt_config((int)ctx->logN, 0, &log_m, &log_e);
-    NttArgs a = make_args(ctx, io, n_limbs, map, lazy_out && ctx->prime_bits <= 50 ? 1 : 0);
+    NttArgs a = make_args(ctx, io, n_limbs, map, 0, lazy_out && ctx->prime_bits <= 50 ? 1 : 0);
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
     if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
     const bool top = subs == 2;
-    const bool lazy = a.mont != 0;
+    const bool lazy = a.lazy != 0;
     FWD_CASE(10, 3) FWD_CASE(10, 4) FWD_CASE(10, 5)
     FWD_CASE(11, 3) FWD_CASE(11, 4) FWD_CASE(11, 5)
     FWD_CASE(12, 3) FWD_CASE(12, 4) FWD_CASE(12, 5)
@@ -462,16 +470,17 @@ int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
 }
 
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
-                   cudaStream_t st) {
+                   cudaStream_t st, int lazy_out) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
     ProfScope ps(ctx, BFHE_K_NTT_INV, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
     int log_m, log_e;
     ntt_config((int)ctx->logN, 1, &log_m, &log_e);
-    NttArgs a = make_args(ctx, io, n_limbs, map, mont);
+    NttArgs a = make_args(ctx, io, n_limbs, map, mont, lazy_out);
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
     if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
     const bool split = subs == 2;
+    const bool lazy = a.lazy != 0;
     INV_CASE(10, 3) INV_CASE(10, 4) INV_CASE(10, 5)
     INV_CASE(11, 3) INV_CASE(11, 4) INV_CASE(11, 5)
     INV_CASE(12, 3) INV_CASE(12, 4) INV_CASE(12, 5)
