@@ -48,8 +48,9 @@ extern "C" {
 #define BFHE_OK 0
 #define BFHE_EINVAL (-1)   /* bad shape, size, parameter or NULL pointer   */
 #define BFHE_ENOMEM (-2)   /* device allocation failed                     */
-#define BFHE_ECUDA (-3)    /* a CUDA call failed (see bfhe_last_cuda_error) */
-#define BFHE_ETIMEOUT (-4) /* a device-side wait gave up                   */
+#define BFHE_ECUDA (-3)    /* a CUDA call failed (bfhe_last_error names it) */
+#define BFHE_ETIMEOUT (-4) /* a device-side wait gave up (reserved: this     */
+                           /* build has no device-side waits)                */
 #define BFHE_ESTATE (-5)   /* call out of order (e.g. encrypt before keygen) */
 
 /* Input-range flags.  Calls are asynchronous, so values are not checked on
@@ -91,6 +92,7 @@ void bfhe_ctx_destroy(bfhe_ctx* ctx);
  * *K_out = K.  Also usable before keygen. */
 int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out);
 
+/* Read and clear the input-range flags (see BFHE_FLAG_* above). */
 int bfhe_check(bfhe_ctx* ctx, void* stream, uint32_t* flags_out);
 
 /* Reserve scratch for batches of up to n ciphertexts in every call (avoids
@@ -319,7 +321,8 @@ int bfhe_ntt_config(uint32_t logN, int inverse, uint32_t log_m, uint32_t log_e, 
  * performed (arrays of BFHE_K_COUNT), then clears the record.  Modmul
  * counts: NTT (N/2) log2 N per limb; modup per coefficient L(L-1)/2 +
  * K(L-1); scale per coefficient of each of 3 polys 2L + 3K + L(L-1)/2 +
- * K(L-1) + K(K-1)/2 + L(K-1); tensor 4 per limb word; inner 2L per word of
+ * K(L-1) + K(K-1)/2 + L(K-1) (both the exact algorithm's count, also when
+ * the fast extension ran); tensor 4 per limb word; inner 2L per word of
  * the Q u P limbs; moddown per coefficient alpha(alpha-1)/2 + L alpha. */
 enum { BFHE_K_NTT_FWD = 0, BFHE_K_NTT_INV = 1, BFHE_K_MODUP = 2, BFHE_K_TENSOR = 3, BFHE_K_SCALE = 4,
        BFHE_K_INNER = 5, BFHE_K_MODDOWN = 6, BFHE_K_COUNT = 7 };
