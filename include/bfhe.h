@@ -82,6 +82,12 @@ typedef struct {
                          /* Sec. 4.1 and 4.3 run bit-level arithmetic at t = 2) */
 } bfhe_params;
 
+/* The parameter rule alone, on the host (no device is touched): the moduli
+ * a context with these parameters would use, in library order (data,
+ * special, auxiliary; at least L + alpha + K entries in primes_out, 64 are
+ * always enough), and K.  Same validation and errors as bfhe_ctx_create. */
+int bfhe_param_primes(const bfhe_params* prm, uint64_t* primes_out, uint32_t* K_out);
+
 /* Create a context on CUDA device `device`.  Builds the moduli, NTT twiddles
  * and RNS constants on the host and uploads them.  *out is set on success. */
 int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** out);

@@ -39,6 +39,7 @@ def load():
     P, S, U32, U64, I = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
     sig = {
         "bfhe_ctx_create": (I, [P, I, P]),
+        "bfhe_param_primes": (I, [P, P, P]),
         "bfhe_ctx_destroy": (None, [P]),
         "bfhe_ctx_primes": (I, [P, P, P]),
         "bfhe_reserve": (I, [P, S]),
@@ -378,3 +379,13 @@ def set_scratch_budget(nbytes):
 
 def scratch_budget():
     return int(load().bfhe_scratch_budget())
+
+
+def param_primes(N, L, alpha, t=65537, prime_bits=50):
+    """Moduli (data, special, auxiliary) and K of the parameter rule, computed on the host."""
+    lib = load()
+    prm = _Params(N, L, alpha, prime_bits, t)
+    buf = (ctypes.c_uint64 * 64)()
+    K = ctypes.c_uint32(0)
+    _check(lib.bfhe_param_primes(ctypes.byref(prm), buf, ctypes.byref(K)))
+    return [int(buf[i]) for i in range(L + alpha + K.value)], K.value

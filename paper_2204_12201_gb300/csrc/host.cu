@@ -368,9 +368,16 @@ int ctx_scratch(bfhe_ctx* ctx, size_t bytes, void** out) {
 }
 
 // ------------------------------------------------------------------ context
-extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** out) {
-    if (!prm || !out) return set_error(BFHE_EINVAL, "null argument");
-    *out = nullptr;
+// The parameter rule (validation, moduli, auxiliary base size) on the host alone.
+struct ParamRule {
+    uint32_t N, logN, L, alpha, bits, K;
+    u64 t;
+    bool batching;
+    std::vector<u64> moduli;   // data, special, auxiliary (not t)
+};
+
+static int param_rule(const bfhe_params* prm, ParamRule* r) {
+    if (!prm) return set_error(BFHE_EINVAL, "null argument");
     const uint32_t N = prm->N;
     if (N < 1024 || N > 32768 || (N & (N - 1))) return set_error(BFHE_EINVAL, "N must be a power of two in [1024, 32768]");
     if (prm->L < 1 || prm->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "L must be in [1, 16]");
@@ -381,25 +388,19 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     const bool batching = t != 2;
     if (batching && (t < 3 || t >= ((u64)1 << 32) || !is_prime(t) || (t - 1) % (2 * (u64)N) != 0))
         return set_error(BFHE_EINVAL, "t must be 2 or a prime < 2^32 with t = 1 mod 2N");
-
-    bfhe_ctx* c = new bfhe_ctx();
-    c->device = device;
-    c->N = N;
-    c->logN = 0;
-    while ((1u << c->logN) < N) ++c->logN;
-    c->L = prm->L;
-    c->alpha = prm->alpha;
-    c->prime_bits = bits;
-    c->t = t;
-    c->batching = batching;
+    r->N = N;
+    r->logN = 0;
+    while ((1u << r->logN) < N) ++r->logN;
+    r->L = prm->L;
+    r->alpha = prm->alpha;
+    r->bits = bits;
+    r->t = t;
+    r->batching = batching;
 
     // primes: data, special, then grow the auxiliary base until B > 2 t N Q (B, Q as exact logs)
-    const int head = (int)(c->L + c->alpha);
+    const int head = (int)(r->L + r->alpha);
     std::vector<u64> all = scan_primes(N, head + 64, bits, t);
-    if ((int)all.size() < head + 2) {
-        delete c;
-        return set_error(BFHE_EINVAL, "not enough NTT-friendly primes");
-    }
+    if ((int)all.size() < head + 2) return set_error(BFHE_EINVAL, "not enough NTT-friendly primes");
     // compare B > 2 t N Q with big integers held as little-endian 32-bit limbs
     auto mul_small = [](std::vector<uint32_t>& a, u64 m) {
         u128 carry = 0;
@@ -423,31 +424,57 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
         return false;
     };
     std::vector<uint32_t> rhs{1};
-    for (uint32_t i = 0; i < c->L; ++i) mul_small(rhs, all[i]);
+    for (uint32_t i = 0; i < r->L; ++i) mul_small(rhs, all[i]);
     mul_small(rhs, 2 * t);
     mul_small(rhs, N);
     std::vector<uint32_t> B{1};
     int K = 0;
     while (!greater(B, rhs)) {
-        if (head + K >= (int)all.size()) {
-            delete c;
-            return set_error(BFHE_EINVAL, "auxiliary base too large");
-        }
+        if (head + K >= (int)all.size()) return set_error(BFHE_EINVAL, "auxiliary base too large");
         mul_small(B, all[head + K]);
         ++K;
     }
-    c->K = (uint32_t)K;
-    if (c->K != c->L + 1) {
-        delete c;
-        return set_error(BFHE_EINVAL, "parameter rule gives K != L + 1 (unsupported)");
-    }
-    for (int i = 0; i < head + K; ++i) {
-        if (all[i] < ((u64)1 << (bits - 1))) {
-            delete c;
-            return set_error(BFHE_EINVAL, "a modulus fell below 2^(prime_bits-1)");
-        }
-    }
-    c->primes.assign(all.begin(), all.begin() + head + K);
+    r->K = (uint32_t)K;
+    if (r->K != r->L + 1) return set_error(BFHE_EINVAL, "parameter rule gives K != L + 1 (unsupported)");
+    for (int i = 0; i < head + K; ++i)
+        if (all[i] < ((u64)1 << (bits - 1))) return set_error(BFHE_EINVAL, "a modulus fell below 2^(prime_bits-1)");
+    r->moduli.assign(all.begin(), all.begin() + head + K);
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_param_primes(const bfhe_params* prm, uint64_t* primes_out, uint32_t* K_out) {
+    if (!primes_out || !K_out) return set_error(BFHE_EINVAL, "null argument");
+    ParamRule r;
+    const int rc = param_rule(prm, &r);
+    if (rc != BFHE_OK) return rc;
+    for (size_t i = 0; i < r.moduli.size(); ++i) primes_out[i] = r.moduli[i];
+    *K_out = r.K;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** out) {
+    if (!prm || !out) return set_error(BFHE_EINVAL, "null argument");
+    *out = nullptr;
+    ParamRule rule;
+    const int prc = param_rule(prm, &rule);
+    if (prc != BFHE_OK) return prc;
+    const uint32_t N = rule.N;
+    const uint32_t bits = rule.bits;
+    const u64 t = rule.t;
+    const bool batching = rule.batching;
+
+    bfhe_ctx* c = new bfhe_ctx();
+    c->device = device;
+    c->N = N;
+    c->logN = rule.logN;
+    c->L = rule.L;
+    c->alpha = rule.alpha;
+    c->prime_bits = bits;
+    c->t = t;
+    c->batching = batching;
+    const int K = (int)rule.K;
+    c->K = rule.K;
+    c->primes = rule.moduli;
     c->primes.push_back(t);
     c->nP = (uint32_t)c->primes.size();
     const uint32_t L = c->L, A = c->alpha, nP = c->nP;

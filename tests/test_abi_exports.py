@@ -76,3 +76,18 @@ def test_error_strings():
     lib, _ = _lib()
     for rc in (0, -1, -2, -3, -4, -5):
         assert lib.bfhe_strerror(rc)
+
+
+def test_library_parameter_rule_matches_the_oracle():
+    """The library's moduli (host-side rule) equal the oracle's for every shape the tests and the
+    workloads use, including t = 2 and 55-bit primes (no GPU involved)."""
+    from oracle.params import Params
+    _, bfhe = _lib()
+    cases = [(1024, 2, 1, 12289, 50), (1024, 3, 1, 65537, 50), (1024, 4, 2, 65537, 50), (1024, 16, 2, 65537, 50),
+             (1024, 2, 1, 65537, 55), (1024, 3, 1, 2, 50), (4096, 2, 1, 65537, 50), (8192, 4, 1, 65537, 50),
+             (16384, 8, 1, 65537, 50), (32768, 16, 2, 65537, 50), (32768, 16, 1, 2, 50), (32768, 4, 2, 65537, 50)]
+    for N, L, alpha, t, bits in cases:
+        primes, K = bfhe.param_primes(N, L, alpha, t, bits)
+        prm = Params(N=N, L=L, alpha=alpha, t=t, prime_bits=bits)
+        assert primes == prm.q + prm.p + prm.b, (N, L, alpha, t, bits)
+        assert K == prm.K == L + 1
