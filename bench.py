@@ -442,8 +442,13 @@ def main():
         if per_limb is not None:
             limbs_per_launch = d_work / max(1, d_launch) / (WL["N"] // 2 * (WL["N"].bit_length() - 1))
             traffic = per_limb * limbs_per_launch
+    hbm = None
+    if traffic is not None and peaks.get("hbm_gbs"):
+        gbs = traffic / (d_ms / max(1, d_launch) / 1e3) / 1e9
+        hbm = {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"]}
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "modmul/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "hbm_side": hbm,
                 "peak_source": "derived: %d SMs x 64 IMAD/clk x %.0f MHz / 16 IMAD slots per 64-bit "
                                "Shoup product (clock from MEASURED_PEAKS.json, %s)"
                                % (props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0), src),
