@@ -170,3 +170,27 @@ def test_genotype_job_full_size_properties():
     g0 = bfv.encrypt(prm, keys, [int(v) for v in G[0]], 10, 0)
     assert np.array_equal(job.last["enc"][0].cpu().numpy(), ct_to_rns(prm, g0))
     ctx.close()
+
+
+def test_benchmark_launch_configuration_sampled_against_the_oracle():
+    """The bench's squaring launches at N = 16384, L = 8: one mul_relin call squares 468 ciphertexts
+    (156 candidates x 3 chains, the tile mod_to_bits forms inside the step), with the context's
+    default (fast) base extension; the first and the last outputs are recomputed by the oracle."""
+    need_gpu()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2204_12201_gb300 import bfhe, inputs
+    prm = Params(**C4)
+    ctx = bfhe.Context(**C4)
+    ctx.keygen(1)
+    assert ctx.fast_extension
+    n = 468
+    y = inputs.slots(901, n, prm.N, hi=prm.t)
+    x = ctx.encrypt(torch.from_numpy(y).cuda(), 902)
+    sq = ctx.mul_relin(x, x)
+    keys = bfv.keygen(prm, 1)
+    for i in (0, n - 1):
+        xi = bfv.encrypt(prm, keys, [int(v) for v in y[i]], 902, i)
+        assert_ct_equal(prm, sq[i:i + 1], [bfv.mul_relin(prm, keys, xi, xi)], "squaring %d of %d" % (i, n))
+    assert np.array_equal(ctx.decrypt(sq).cpu().numpy(), (y * y) % prm.t)
+    ctx.close()
