@@ -354,3 +354,24 @@ def test_fast_extension_needs_small_moduli():
     assert not P.ctx.fast_extension
     with pytest.raises(bfhe.BfheError):
         P.ctx.set_fast_extension(True)
+
+
+def test_mod_to_sint_at_t65537():
+    """Listing 9 at the workloads' t = 65537 with s = 17 (the least s with 2^s >= t), select mode,
+    two candidates per conversion: x in {t-2, t-1} (negative) and its shifted range."""
+    P = pair("C1", C1)
+    prm = P.prm
+    t, s = prm.t, 17
+    xs = inputs.slots(33, 1, prm.N, lo=t - 2, hi=t)[0]
+    x = P.enc(xs, 141, 0)
+    shift = ((1 << s) - t) % t
+    pos_r = (t - 2, t - 1)
+    neg_r = ((t - 2 + shift) % t, (t - 1 + shift) % t)
+    assert neg_r[0] <= neg_r[1]
+    ev = bridge.Evaluator(prm, P.keys)
+    want = ev.mod_to_sint(x, s, range(pos_r[0], pos_r[1] + 1), range(neg_r[0], neg_r[1] + 1), bridge.SELECT)
+    P.ctx.op_counts(reset=True)
+    got = P.ctx.mod_to_sint(cts_to_device(prm, [x]), s, pos_r, neg_r, bridge.SELECT)
+    for k in range(s):
+        assert_ct_equal(prm, got[k], [want[k]], "mod_to_sint bit %d" % k)
+    assert P.ctx.op_counts()[:3] == ev.counts()
