@@ -124,50 +124,56 @@ __global__ void k_pointwise(const u64* A, const u64* B, u64* out, int n, int pol
 }
 
 // tensor in place: X[c][0..3] = (a0, a1, b0, b1) -> X[c][0..2] = (d0, d1, d2), Montgomery factor 2^-64
+// Each thread takes two consecutive words (one 16-byte load per operand; N is even, so a pair never
+// straddles limbs, and every limb starts 16-byte aligned).
+__device__ __forceinline__ void tensor_word(u64 a0, u64 a1, u64 b0, u64 b1, u64 q, u64 qinv, u64& d0, u64& d1,
+                                            u64& d2) {
+    d0 = redc(__umul64hi(a0, b0), a0 * b0, q, qinv);
+    u64 hi = 0, lo = 0;
+    mac128(hi, lo, a0, b1);
+    mac128(hi, lo, a1, b0);
+    d1 = redc(hi, lo, q, qinv);
+    d2 = redc(__umul64hi(a1, b1), a1 * b1, q, qinv);
+}
+
 __global__ void k_tensor(u64* X, int n, int LK, LimbMap map, PrimeTab tab, int N) {
-    const size_t plane = (size_t)LK * N;
-    const size_t total = (size_t)n * plane;
+    const size_t plane = (size_t)LK * N, half = plane / 2;
+    const size_t total = (size_t)n * half;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t c = idx / plane, off = idx % plane;
-        const int limb = (int)(off / N);
-        const int pi = map(limb);
+        const size_t c = idx / half, off = (idx % half) * 2;
+        const int pi = map((int)(off / N));
         const u64 q = tab.q[pi], qinv = tab.qinv[pi];
-        u64* x = X + c * 4 * plane + off;
-        const u64 a0 = x[0], a1 = x[plane], b0 = x[2 * plane], b1 = x[3 * plane];
-        const u64 d0 = redc(__umul64hi(a0, b0), a0 * b0, q, qinv);
-        u64 hi = 0, lo = 0;
-        mac128(hi, lo, a0, b1);
-        mac128(hi, lo, a1, b0);
-        const u64 d1 = redc(hi, lo, q, qinv);
-        const u64 d2 = redc(__umul64hi(a1, b1), a1 * b1, q, qinv);
-        x[0] = d0;
-        x[plane] = d1;
-        x[2 * plane] = d2;
+        ulonglong2* x = reinterpret_cast<ulonglong2*>(X + c * 4 * plane + off);
+        const size_t p2 = half;   // one plane in 16-byte units
+        const ulonglong2 a0 = x[0], a1 = x[p2], b0 = x[2 * p2], b1 = x[3 * p2];
+        u64 e0, e1, e2, f0, f1, f2;
+        tensor_word(a0.x, a1.x, b0.x, b1.x, q, qinv, e0, e1, e2);
+        tensor_word(a0.y, a1.y, b0.y, b1.y, q, qinv, f0, f1, f2);
+        x[0] = make_ulonglong2(e0, f0);
+        x[p2] = make_ulonglong2(e1, f1);
+        x[2 * p2] = make_ulonglong2(e2, f2);
     }
 }
 
 // squaring: X[c][0..1] = (a0, a1) -> X[c][0..2] = (a0^2, 2 a0 a1, a1^2), same sums as the general tensor
 __global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, int N) {
-    const size_t plane = (size_t)LK * N;
-    const size_t total = (size_t)n * plane;
+    const size_t plane = (size_t)LK * N, half = plane / 2;
+    const size_t total = (size_t)n * half;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t c = idx / plane, off = idx % plane;
-        const int limb = (int)(off / N);
-        const int pi = map(limb);
+        const size_t c = idx / half, off = (idx % half) * 2;
+        const int pi = map((int)(off / N));
         const u64 q = tab.q[pi], qinv = tab.qinv[pi];
-        u64* x = X + c * 4 * plane + off;
-        const u64 a0 = x[0], a1 = x[plane];
-        const u64 d0 = redc(__umul64hi(a0, a0), a0 * a0, q, qinv);
-        u64 hi = 0, lo = 0;
-        mac128(hi, lo, a0, a1);
-        mac128(hi, lo, a1, a0);
-        const u64 d1 = redc(hi, lo, q, qinv);
-        const u64 d2 = redc(__umul64hi(a1, a1), a1 * a1, q, qinv);
-        x[0] = d0;
-        x[plane] = d1;
-        x[2 * plane] = d2;
+        ulonglong2* x = reinterpret_cast<ulonglong2*>(X + c * 4 * plane + off);
+        const size_t p2 = half;
+        const ulonglong2 a0 = x[0], a1 = x[p2];
+        u64 e0, e1, e2, f0, f1, f2;
+        tensor_word(a0.x, a1.x, a0.x, a1.x, q, qinv, e0, e1, e2);
+        tensor_word(a0.y, a1.y, a0.y, a1.y, q, qinv, f0, f1, f2);
+        x[0] = make_ulonglong2(e0, f0);
+        x[p2] = make_ulonglong2(e1, f1);
+        x[2 * p2] = make_ulonglong2(e2, f2);
     }
 }
 
@@ -796,9 +802,9 @@ int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, int square, cudaStream_t s
     ProfScope ps(ctx, BFHE_K_TENSOR, st, 4.0 * n * (ctx->L + ctx->K) * ctx->N);
     const int LK = (int)(ctx->L + ctx->K);
     if (square)
-        LAUNCH(k_tensor_sq, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
+        LAUNCH(k_tensor_sq, (size_t)n * LK * ctx->N / 2, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
     else
-        LAUNCH(k_tensor, (size_t)n * LK * ctx->N, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
+        LAUNCH(k_tensor, (size_t)n * LK * ctx->N / 2, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
     return BFHE_OK;
 }
 
