@@ -56,3 +56,26 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2)
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_figure_follows_the_profiled_sources(tmp_path, monkeypatch):
+    """bench.py reads the NTT's DRAM bytes per limb from the committed ncu summary only while the
+    transform sources hash to the value recorded there."""
+    sys.path.insert(0, ROOT)
+    import bench
+    got = bench.ntt_traffic_per_limb("k_ntt_fwd")
+    text = open(os.path.join(ROOT, "profiles", "k_ntt_fwd_traffic_genotype_N16384.md")).read()
+    recorded = float(text.split("`dram_bytes_per_limb`: `")[1].split("`")[0])
+    assert got in (None, recorded)   # None once the transform sources change, until re-profiled
+    # a summary whose recorded hash differs gives no figure
+    fake = tmp_path / "profiles"
+    fake.mkdir()
+    (fake / "k_ntt_fwd_traffic_genotype_N16384.md").write_text(
+        "- `dram_bytes_per_limb`: `1`\n- `sources_sha256`: `00` (other sources)\n")
+    csrc = tmp_path / "paper_2204_12201_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("ntt.cu", "common.cuh"):
+        (csrc / f).write_bytes(open(os.path.join(ROOT, "paper_2204_12201_gb300", "csrc", f), "rb").read())
+    monkeypatch.setattr(bench.os.path, "abspath", lambda p: str(tmp_path / "bench.py"))
+    assert bench.ntt_traffic_per_limb("k_ntt_fwd") is None
+    assert bench.ntt_traffic_per_limb("k_other") is None
