@@ -7,11 +7,8 @@
 // -1}[w mod 3], centred binomial popcount(w & (2^21-1)) - popcount((w >> 21)
 // & (2^21-1)).
 //
-// Exact RNS: the multiply lifts each input coefficient to the centred range
-// and extends it exactly to the auxiliary base by Garner's mixed-radix
-// conversion (no approximate fast base conversion), and scale-and-round
-// computes round(t d / Q) as y = (t d - r) / Q with r the centred residue of
-// t d mod Q, again by two exact extensions (Q -> B for r, B -> Q for y).
+// The exact base extensions (lift, scale-and-round, mod-down, decryption's
+// last step) are in ext.cu.
 #include "kernels.cuh"
 
 namespace {
@@ -229,265 +226,6 @@ __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, in
 #pragma unroll
                 for (int j = 0; j < L; ++j) buf[b][j] = buf[b + 1][j];
         }
-    }
-}
-
-// ---------------------------------------------------------------- exact base extension
-// Inputs x_i may be lazy (< 2 s_i); digits come out canonical.  Inner steps keep
-// u in [0, 2 s_i): u + s_i - v_j < 3 s_i goes straight into a lazy Shoup product.
-template <int NS>
-__device__ __forceinline__ bool garner(const u64 (&x)[NS], const ExtDesc& d, u64 (&v)[NS]) {
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const u64 si = d.src_q[i];
-        u64 u = x[i];
-#pragma unroll
-        for (int j = 0; j < i; ++j) {
-            u64 vj = v[j];
-            vj = vj >= si ? vj - si : vj;
-            u = shoup_lazy(u + si - vj, d.ginv[i * NS + j], d.ginv_s[i * NS + j], si);
-        }
-        u = u >= si ? u - si : u;
-        v[i] = u;
-    }
-    int state = 0;
-#pragma unroll
-    for (int i = NS - 1; i >= 0; --i) {
-        const u64 h = d.hdig[i];
-        if (state == 0) state = v[i] > h ? 1 : (v[i] < h ? -1 : 0);
-    }
-    return state > 0;   // x > (S-1)/2: the centred value is x - S
-}
-
-// value mod T_j of the centred integer with digits v (SMALL: T may be far below the sources).
-// Without SMALL every digit is < 2 T_j, so Horner runs lazily below 4 T_j.
-template <int NS, bool SMALL>
-__device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtDesc& d, int j) {
-    const u64 T = d.dst_q[j];
-    u64 acc;
-    if (SMALL) {
-        const u64 mu = d.dst_mu[j];
-        acc = reduce64(v[NS - 1], T, mu);
-#pragma unroll
-        for (int i = NS - 2; i >= 0; --i) {
-            acc = shoup(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T);
-            acc = add_mod(acc, reduce64(v[i], T, mu), T);
-        }
-    } else {
-        acc = v[NS - 1];
-#pragma unroll
-        for (int i = NS - 2; i >= 0; --i)
-            acc = shoup_lazy(acc, d.radix[j * NS + i], d.radix_s[j * NS + i], T) + v[i];
-        const u64 T2 = T << 1;
-        acc = acc >= T2 ? acc - T2 : acc;
-        acc = acc >= T ? acc - T : acc;
-    }
-    if (neg) acc = sub_mod(acc, d.smod[j], T);
-    return acc;
-}
-
-// Guarded fast exact extension (all moduli below 2^50), first half: y_i = [x_i (S/s_i)^-1]_{s_i} split
-// into 26-bit limbs, and v = round(sum_i y_i / s_i) from the 64.64 fixed-point sum of
-// floor(y_i floor(2^128/s_i) / 2^64) (each term at most 2 units below y_i 2^64 / s_i).  Returns false
-// when the fraction lies within 2n + 2 units of 1/2: then the caller takes the exact mixed-radix path.
-template <int NS>
-__device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, uint32_t (&y0)[NS],
-                                          uint32_t (&y1)[NS], int& v) {
-    u64 lo = 0, hi = 0;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const u64 s = d.src_q[i];
-        const u64 y = shoup(x[i], d.qhinv[i], d.qhinv_s[i], s);
-        y0[i] = (uint32_t)(y & 0x3FFFFFFull);
-        y1[i] = (uint32_t)(y >> 26);
-        const u64 term = y * d.g_hi[i] + __umul64hi(y, d.g_lo[i]);
-        lo += term;
-        hi += lo < term ? 1ull : 0ull;
-    }
-    const u64 half = 1ull << 63;
-    if (lo > half) {
-        v = (int)hi + 1;
-        return true;
-    }
-    if (lo + (u64)(2 * NS + 2) <= half) {
-        v = (int)hi;
-        return true;
-    }
-    return false;
-}
-
-// second half: sum_i y_i [(S/s_i) 2^64]_{T_j} with the 26-bit limb products accumulated in four 64-bit
-// words (no carries below 2^13 sources), one Montgomery reduction, minus [v S]_{T_j}; canonical result
-template <int NS>
-__device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_t (&y1)[NS], int v, const ExtDesc& d,
-                                         int j) {
-    const uint2* c = reinterpret_cast<const uint2*>(d.c26) + (size_t)j * NS;   // (low, high) limb pairs, 8-byte aligned
-    u64 p00 = 0, p01 = 0, p10 = 0, p11 = 0;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) {
-        const uint2 cc = __ldg(c + i);
-        const uint32_t c0 = cc.x, c1 = cc.y;
-        p00 += (u64)y0[i] * c0;
-        p01 += (u64)y0[i] * c1;
-        p10 += (u64)y1[i] * c0;
-        p11 += (u64)y1[i] * c1;
-    }
-    const u64 mid = p01 + p10;                       // weight 2^26
-    u64 lo = p00 + (mid << 26);
-    u64 hi = (mid >> 38) + (lo < p00 ? 1ull : 0ull);
-    const u64 top = p11 << 52;                       // weight 2^52
-    lo += top;
-    hi += (p11 >> 12) + (lo < top ? 1ull : 0ull);
-    const u64 T = d.dst_q[j];
-    return sub_mod(redc(hi, lo, T, d.dst_qinv[j]), d.vS[(size_t)j * (NS + 1) + v], T);
-}
-
-// X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
-template <int NS, bool FAST>
-__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
-                        uint32_t* flags) {
-    const size_t total = (size_t)n * slots * N;
-    const int LK = NS + K;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const size_t pp = idx / N;
-        const size_t c = pp / slots;
-        const int slot = (int)(pp % slots);
-        const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)NS * N + k;
-        u64* dst = X + (c * 4 + slot) * (size_t)LK * N + k;
-        u64 x[NS];
-        bool bad = false;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            x[i] = src[(size_t)i * N];
-            dst[(size_t)i * N] = x[i];
-            bad |= x[i] >= ext.src_q[i];
-        }
-        if (bad) atomicOr(flags, BFHE_FLAG_RESIDUE);
-        if constexpr (FAST) {
-            uint32_t y0[NS], y1[NS];
-            int vv = 0;
-            if (fast_prep<NS>(x, ext, y0, y1, vv)) {
-                for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = fast_eval<NS>(y0, y1, vv, ext, j);
-                continue;
-            }
-        }
-        u64 v[NS];
-        const bool neg = garner<NS>(x, ext, v);
-        for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = ext_eval<NS, false>(v, neg, ext, j);
-    }
-}
-
-// scale-and-round of the tensor (X slots 0..2, Q u B limbs) into C3 [n][3][L][N]
-template <int NS, int KS, bool FAST>
-__global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* tmod, int nP,
-                        const u64* Qinv_b, const u64* bq, int N) {
-    const size_t total = (size_t)n * 3 * N;
-    constexpr int LK = NS + KS;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const size_t cp = idx / N;
-        const size_t c = cp / 3;
-        const int comp = (int)(cp % 3);
-        const u64* d = X + (c * 4 + comp) * (size_t)LK * N + k;
-        u64 r[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const u64 qi = eQB.src_q[i];
-            r[i] = shoup_lazy(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);   // [t d]_{q_i}, < 2 q_i
-        }
-        // r -> B (centred), then y = (t d - r) / Q in B
-        u64 y[KS];
-        {
-            uint32_t r0[NS], r1[NS];
-            int vv = 0;
-            bool fast = false;
-            if constexpr (FAST) fast = fast_prep<NS>(r, eQB, r0, r1, vv);
-            u64 v[NS];
-            bool neg = false;
-            if (!fast) neg = garner<NS>(r, eQB, v);
-#pragma unroll
-            for (int j = 0; j < KS; ++j) {
-                const u64 bj = bq[j];
-                const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
-                const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);   // < 2 b_j
-                u64 rb;
-                if constexpr (FAST) rb = fast ? fast_eval<NS>(r0, r1, vv, eQB, j) : ext_eval<NS, false>(v, neg, eQB, j);
-                else rb = ext_eval<NS, false>(v, neg, eQB, j);
-                y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
-            }
-        }
-        // y -> Q (centred)
-        u64* o = C3 + cp * (size_t)NS * N + k;
-        if constexpr (FAST) {
-            uint32_t y0[KS], y1[KS];
-            int vy = 0;
-            if (fast_prep<KS>(y, eBQ, y0, y1, vy)) {
-#pragma unroll
-                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS>(y0, y1, vy, eBQ, i);
-                continue;
-            }
-        }
-        u64 w[KS];
-        const bool negy = garner<KS>(y, eBQ, w);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) o[(size_t)i * N] = ext_eval<KS, false>(w, negy, eBQ, i);
-    }
-}
-
-// out[c][comp] = C3[c][comp] + round(W / P) mod Q, W over Q u P (coefficient form)
-template <int NA>
-__global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, ExtDesc ePQ, const u64* Pinv,
-                          const u64* qtab, int N) {
-    const size_t total = (size_t)n * 2 * N;
-    const int QP = L + NA;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const size_t cp = idx / N;
-        const size_t c = cp >> 1;
-        const int comp = (int)(cp & 1);
-        const u64* w = W + cp * (size_t)QP * N + k;
-        u64 x[NA], v[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) x[a] = w[(size_t)(L + a) * N];
-        const bool neg = garner<NA>(x, ePQ, v);
-        const u64* cin = C3 + (c * 3 + comp) * (size_t)L * N + k;
-        u64* o = out + cp * (size_t)L * N + k;
-        for (int i = 0; i < L; ++i) {
-            const u64 qi = qtab[i];
-            const u64 e = ext_eval<NA, false>(v, neg, ePQ, i);
-            const u64 y = shoup(sub_mod(w[(size_t)i * N], e, qi), Pinv[i], Pinv[L + i], qi);
-            o[(size_t)i * N] = add_mod(cin[(size_t)i * N], y, qi);
-        }
-    }
-}
-
-// decrypt: m = [-r Q^-1]_t with r the centred [t (c0 + c1 s)]_Q
-template <int NS>
-__global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc eQt, const u64* tmod, int nP,
-                             u64 Qinv_t, int N, uint32_t* flags) {
-    const size_t total = (size_t)n * N;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const size_t c = idx / N;
-        u64 r[NS], v[NS];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const u64 qi = eQt.src_q[i];
-            const u64 c0 = ct[(c * 2 * NS + i) * N + k];
-            if (c0 >= qi) atomicOr(flags, BFHE_FLAG_RESIDUE);
-            const u64 vi = add_mod(V[(c * NS + i) * N + k], c0, qi);
-            r[i] = shoup(vi, tmod[i], tmod[nP + i], qi);
-        }
-        const bool neg = garner<NS>(r, eQt, v);
-        const u64 t = eQt.dst_q[0];
-        const u64 rho = ext_eval<NS, true>(v, neg, eQt, 0);        // [r]_t
-        const u64 mneg = rho == 0 ? 0 : t - rho;
-        M[idx] = (mneg * Qinv_t) % t;
     }
 }
 
@@ -817,37 +555,6 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
     return BFHE_OK;
 }
 
-template <int NS>
-int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
-    const size_t work = (size_t)n * slots * ctx->N;
-    if (ctx->fast_ext && ctx->ext_QB.fast_ok)
-        LAUNCH((k_modup<NS, true>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
-    else
-        LAUNCH((k_modup<NS, false>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
-    return BFHE_OK;
-}
-
-template <int NS>
-int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
-    const size_t work = (size_t)n * 3 * ctx->N;
-    const u64* bq = ctx->tab.q + ctx->L + ctx->alpha;
-    if (ctx->fast_ext && ctx->ext_QB.fast_ok && ctx->ext_BQ.fast_ok)
-        LAUNCH((k_scale<NS, NS + 1, true>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
-               ctx->d_Qinv_b, bq, (int)ctx->N);
-    else
-        LAUNCH((k_scale<NS, NS + 1, false>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
-               ctx->d_Qinv_b, bq, (int)ctx->N);
-    return BFHE_OK;
-}
-
-template <int NS>
-int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
-    const size_t work = (size_t)n * ctx->N;
-    LAUNCH(k_dec_finish<NS>, work, V, ct, M, n, ctx->ext_Qt, ctx->d_tmod, (int)ctx->nP, ctx->Qinv_t, (int)ctx->N,
-           ctx->d_flags);
-    return BFHE_OK;
-}
-
 #define SWITCH_L(Lv, FN, ...)                                                                                  \
     switch (Lv) {                                                                                              \
         case 1: return FN<1>(__VA_ARGS__);                                                                     \
@@ -872,37 +579,6 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
 int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
     ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
     SWITCH_L(ctx->L, run_inner, ctx, Dg, W, n, st)
-}
-
-int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
-    const double L_ = ctx->L, K_ = ctx->K;
-    ProfScope ps(ctx, BFHE_K_MODUP, st, (double)slots * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
-    SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, slots, st)
-}
-
-int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
-    if (ctx->K != ctx->L + 1) return set_error(BFHE_EINVAL, "auxiliary base must have L+1 primes");
-    const double L_ = ctx->L, K_ = ctx->K;
-    ProfScope ps(ctx, BFHE_K_SCALE, st,
-                 3.0 * n * ctx->N * (2 * L_ + 3 * K_ + L_ * (L_ - 1) / 2 + K_ * (L_ - 1) + K_ * (K_ - 1) / 2 + L_ * (K_ - 1)));
-    SWITCH_L(ctx->L, run_scale, ctx, X, C3, n, st)
-}
-
-int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st) {
-    const double A_ = ctx->alpha;
-    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_));
-    const size_t work = (size_t)n * 2 * ctx->N;
-    if (ctx->alpha == 1)
-        LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
-    else if (ctx->alpha == 2)
-        LAUNCH(k_moddown<2>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
-    else
-        return set_error(BFHE_EINVAL, "alpha must be 1 or 2");
-    return BFHE_OK;
-}
-
-int launch_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
-    SWITCH_L(ctx->L, run_dec_finish, ctx, V, ct, M, n, st)
 }
 
 int launch_permute(const bfhe_ctx* ctx, const u64* in, u64* out, int n, int scatter, cudaStream_t st) {
