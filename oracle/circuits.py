@@ -1,8 +1,8 @@
 """Bit-level circuits built from the oracle's gates (test infrastructure only).
 
-The paper builds comparison, addition and multiplication "using standard
-combinational arithmetic circuit design" (Sec. 3.1) without giving netlists.
-These are this build's netlists, written as plain gate expressions; bits are
+Sec. 3.1 leaves comparison, addition and multiplication to ordinary
+combinational circuits over its gates and gives no netlists.  These are the
+netlists chosen here, written as plain gate expressions; bits are
 little-endian lists of ciphertexts (bit 0 first).
 
 * ripple-carry adder: p_i = a_i b_i, u_i = a_i XOR b_i, q_i = c_i u_i,

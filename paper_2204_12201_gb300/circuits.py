@@ -1,8 +1,7 @@
 """Levelised bit-level circuits over the bfhe gate-level entry point.
 
-The paper builds comparison, addition and multiplication "using standard
-combinational arithmetic circuit design" over the homomorphic gates of
-Sec. 3.1 and does not give netlists.  A circuit here is a DAG of two node
+Sec. 3.1 leaves comparison, addition and multiplication over its
+homomorphic gates to ordinary combinational circuits and gives no netlists.  A circuit here is a DAG of two node
 kinds: MUL (one relinearised ciphertext product) and LIN (a linear
 combination with coefficients in -2..2 plus a multiple of the constant 1).
 Every gate equation of Sec. 3.1 is one MUL and one LIN (NOT is a LIN).
