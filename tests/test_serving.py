@@ -127,6 +127,29 @@ def test_sequential_baseline_matches():
     assert s["requests"] == 6 and s["p99_s"] >= s["p50_s"] > 0
 
 
+def test_admission_is_first_come_first_served():
+    """A request is admitted no earlier than its arrival, and in arrival order: a small request behind
+    a large one that does not fit yet waits for it (no overtaking)."""
+    reqs = serving.poisson_stream(7, 12, rate=3000.0, ring_degrees=(4096,), depth=(1, 6), cts=(1, 4))
+    b = FakeBackend()
+    clk = FakeClock()
+    srv = serving.Server(b, mem_budget_bytes=0)
+    srv.budget = 2 * max(srv.need(r) for r in reqs)
+    done = srv.run(copy.deepcopy(reqs), clock=clk, sleep=clk.sleep)
+    admitted = sorted(done, key=lambda r: (r.t_admit, r.arrival))
+    assert [r.rid for r in admitted] == [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert all(r.t_admit >= r.arrival for r in done)
+
+
+def test_summary_percentiles():
+    reqs = [serving.Request(rid=i, N=4096, depth=1, n=2, arrival=float(i), seed=i) for i in range(100)]
+    for i, r in enumerate(reqs):
+        r.t_done = r.arrival + (i + 1) / 100.0           # latencies 0.01 .. 1.00 s
+    s = serving.summarize(reqs)
+    assert abs(s["p50_s"] - 0.505) < 1e-9 and abs(s["p99_s"] - 0.9901) < 1e-9
+    assert s["requests"] == 100 and abs(s["mul_relin_per_s"] - 200 / (99 + 1.0)) < 1e-9
+
+
 @pytest.mark.gpu
 def test_gpu_result_is_the_same_alone_and_in_the_mix():
     """Bit-exact (the tolerance of every parity check here is equality)."""
