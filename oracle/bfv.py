@@ -42,8 +42,17 @@ def _zeta_table(prm):
     return tab
 
 
+def _mulmod(a, b, t):
+    """a * b mod t elementwise, exact in int64 for values in [0, t) and t < 2^32: b is split into
+    16-bit halves, so no intermediate reaches 2^48."""
+    lo = (a * (b & 0xFFFF)) % t
+    hi = (a * (b >> 16)) % t
+    return (lo + ((hi << 16) % t)) % t
+
+
 def decode_poly(prm, m):
-    """Slots of a plaintext polynomial: y_j = m(zeta^(2j+1)) mod t (plain evaluation)."""
+    """Slots of a plaintext polynomial: y_j = m(zeta^(2j+1)) mod t (plain evaluation).
+    Every product is reduced mod t before the sum over k (N terms below t < 2^32 sum below 2^47)."""
     N, t = prm.N, prm.t
     tab = _zeta_table(prm)
     mv = np.array([x % t for x in m], dtype=np.int64)
@@ -53,7 +62,7 @@ def decode_poly(prm, m):
     for j0 in range(0, N, chunk):
         j = np.arange(j0, min(N, j0 + chunk), dtype=np.int64)
         e = ((2 * j[:, None] + 1) * k[None, :]) % (2 * N)
-        out[j0:j0 + len(j)] = (tab[e] * mv[None, :]).sum(axis=1) % t
+        out[j0:j0 + len(j)] = _mulmod(tab[e], mv[None, :], t).sum(axis=1) % t
     return [int(x) for x in out]
 
 
@@ -68,7 +77,7 @@ def encode_slots(prm, y):
     for k0 in range(0, N, chunk):
         k = np.arange(k0, min(N, k0 + chunk), dtype=np.int64)
         e = (-(2 * j[None, :] + 1) * k[:, None]) % (2 * N)
-        out[k0:k0 + len(k)] = (tab[e] * yv[None, :]).sum(axis=1) % t
+        out[k0:k0 + len(k)] = _mulmod(tab[e], yv[None, :], t).sum(axis=1) % t
     ninv = inv(N, t)
     return [int(x) * ninv % t for x in out]
 

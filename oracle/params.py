@@ -13,6 +13,7 @@ pick the rest (Sec. 4.1).  This build fixes the remaining choices as follows:
   in the centred range of the moduli QB and B respectively;
 * Delta = floor(Q / t); the slot root is zeta = g^((t-1)/2N) mod t with g the
   least primitive root of t;
+* t < 2^32, the plaintext moduli the library accepts;
 * t = 2 (Sec. 4.1 and 4.3 run the bit-level benchmarks with t = 2 as well):
   no batching (2 is not 1 mod 2N), so plaintexts are polynomials with
   coefficients mod 2 and there is no slot root.
@@ -63,6 +64,8 @@ class Params:
         self.batching = t != 2
         if self.batching and (not is_prime(t) or (t - 1) % (2 * N)):
             raise ValueError("batching needs a prime t = 1 mod 2N (or t = 2 without batching)")
+        if t >= 1 << 32:
+            raise ValueError("t must be below 2^32 (the slot transforms reduce products of two values below t)")
         head = scan_primes(N, self.L + self.alpha, self.prime_bits, exclude=(t,))
         self.q = head[: self.L]
         self.p = head[self.L:]

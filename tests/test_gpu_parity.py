@@ -28,6 +28,7 @@ MID = dict(N=16384, L=2, alpha=1)          # N = 16384: split-half forward NTT, 
 C4 = dict(N=16384, L=8, alpha=1)           # the benchmark's parameters
 L16 = dict(N=1024, L=16, alpha=2)          # the largest limb count, two special primes (the bridge workload's)
 BIG_Q = dict(N=1024, L=2, alpha=1, prime_bits=55)   # primes above 2^50: the multiply's transforms stay canonical
+BIG_T = dict(N=1024, L=3, alpha=1, t=4294957057)    # the largest t = 1 mod 2048 below 2^32: (t - 1)^2 > 2^63
 
 
 class Pair:
@@ -57,7 +58,7 @@ def pair(name, cfg):
 
 
 @pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("ALPHA2", ALPHA2), ("WIDE", WIDE),
-                                      ("LOW_T", LOW_T)])
+                                      ("LOW_T", LOW_T), ("BIG_T", BIG_T)])
 def test_params_and_keys(name, cfg):
     P = pair(name, cfg)
     prm = P.prm
@@ -97,7 +98,7 @@ def test_ntt_convolution(name, cfg):
     assert np.array_equal(da.cpu().numpy()[0], np.array(a, dtype=np.int64))
 
 
-@pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("WIDE", WIDE)])
+@pytest.mark.parametrize("name,cfg", [("C1", C1), ("SMALL", SMALL), ("WIDE", WIDE), ("BIG_T", BIG_T)])
 def test_encrypt_decrypt(name, cfg):
     P = pair(name, cfg)
     prm = P.prm
@@ -135,7 +136,7 @@ def test_linear_ops():
 
 @pytest.mark.parametrize("name,cfg,n", [("C1", C1, 3), ("SMALL", SMALL, 2), ("ALPHA2", ALPHA2, 2),
                                         ("WIDE", WIDE, 1), ("LOW_T", LOW_T, 2), ("MID", MID, 1),
-                                        ("L16", L16, 2), ("BIG_Q", BIG_Q, 2)])
+                                        ("L16", L16, 2), ("BIG_Q", BIG_Q, 2), ("BIG_T", BIG_T, 2)])
 def test_mul_relin(name, cfg, n):
     P = pair(name, cfg)
     prm = P.prm
@@ -147,6 +148,23 @@ def test_mul_relin(name, cfg, n):
     assert_ct_equal(prm, got, want, "mul_relin")
     dec = P.ctx.decrypt(got).cpu().numpy()
     assert np.array_equal(dec, (y[:n] * y[n:]) % prm.t)
+
+
+def test_large_t_plain_and_scalar():
+    """Slot encoding of a public vector (an NTT over t) and the largest scalar at t just below 2^32."""
+    P = pair("BIG_T", BIG_T)
+    prm, ctx = P.prm, P.ctx
+    t = prm.t
+    y = inputs.slots(19, 2, prm.N, lo=t - 1000, hi=t)
+    a = [P.enc(y[0], 33, 0)]
+    da = cts_to_device(prm, a)
+    w = y[1]
+    got = ctx.mul_plain(da, torch.from_numpy(w[None]).cuda())
+    assert_ct_equal(prm, got, [bfv.mul_plain(prm, a[0], [int(v) for v in w])], "mul_plain")
+    want = np.array([int(u) * int(v) % t for u, v in zip(y[0], w)], dtype=np.int64)   # exact: no int64 product
+    assert np.array_equal(ctx.decrypt(got).cpu().numpy()[0], want)
+    assert_ct_equal(prm, ctx.mul_scalar(da, t - 1), [bfv.mul_scalar(prm, a[0], t - 1)], "mul_scalar")
+    assert_ct_equal(prm, ctx.add_const(da, t - 1), [bfv.add_const(prm, a[0], t - 1)], "add_const")
 
 
 def test_mul_relin_edge_values():

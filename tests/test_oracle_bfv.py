@@ -42,6 +42,63 @@ def test_decode_is_evaluation_at_odd_roots(cfg):
         assert _brute_eval(prm, mm) == y
 
 
+# the largest plaintext moduli the library accepts: primes t = 1 mod 2048 just below 2^31 and 2^32;
+# at the second, (t - 1)^2 exceeds 2^63, so a product or a sum of products in int64 would wrap
+LARGE_T = (2147473409, 4294957057)
+
+
+def _brute_eval_table(prm, m):
+    """y_j = sum_k m_k zeta^((2j+1)k) mod t with Python integers (no overflow), powers from a table."""
+    t, N = prm.t, prm.N
+    zp = [pow(prm.zeta, e, t) for e in range(2 * N)]
+    return [sum(mk * zp[(2 * j + 1) * k % (2 * N)] for k, mk in enumerate(m)) % t for j in range(N)]
+
+
+@pytest.mark.parametrize("t", LARGE_T)
+def test_slot_transforms_are_exact_at_large_t(t):
+    """Sec. 2.3 batching at the largest t below 2^32: decode against big-integer evaluation, encode as its
+    inverse, with inputs near t - 1 where products are largest."""
+    prm = Params(N=1024, L=1, alpha=1, t=t)
+    assert pow(prm.zeta, 2 * prm.N, t) == 1 and pow(prm.zeta, prm.N, t) == t - 1
+    rng = random.Random(t)
+    m = [t - 1 - rng.randrange(16) for _ in range(prm.N)]
+    assert bfv.decode_poly(prm, m) == _brute_eval_table(prm, m)
+    y = [rng.randrange(t) for _ in range(prm.N)]
+    mm = bfv.encode_slots(prm, y)
+    assert all(0 <= x < t for x in mm)
+    assert _brute_eval_table(prm, mm) == y
+    # a plain int64 product-sum (no reduction per product) wraps here: the pin can tell the difference
+    if (t - 1) ** 2 >= 1 << 63:
+        import numpy as np
+        with np.errstate(over="ignore"):
+            a = np.array([t - 1] * 4, dtype=np.int64)
+            assert int((a * a).sum() % t) != 4 * (t - 1) ** 2 % t
+
+
+def test_parameter_rule_rejects_t_from_2_to_the_32():
+    # 2^32 + 12 * 2^11 + 1 is a prime = 1 mod 2048: batching-friendly at N = 1024 but above the bound
+    t = (1 << 32) + 12 * (1 << 11) + 1
+    from oracle.nt import is_prime
+    assert is_prime(t)
+    with pytest.raises(ValueError):
+        Params(N=1024, L=1, alpha=1, t=t)
+
+
+@pytest.mark.parametrize("t", LARGE_T)
+def test_multiply_decrypts_at_large_t(t):
+    prm = Params(N=1024, L=3, alpha=1, t=t)
+    keys = bfv.keygen(prm, 12)
+    rng = random.Random(8)
+    y1 = [rng.randrange(t) for _ in range(prm.N)]
+    y2 = [rng.randrange(t) for _ in range(prm.N)]
+    a = bfv.encrypt(prm, keys, y1, 2, 0)
+    b = bfv.encrypt(prm, keys, y2, 2, 1)
+    assert bfv.decrypt(prm, keys, a) == y1
+    c = bfv.mul_relin(prm, keys, a, b)
+    assert bfv.decrypt(prm, keys, c) == [x * y % t for x, y in zip(y1, y2)]
+    assert bfv.noise_budget(prm, keys, c) > 0
+
+
 @pytest.mark.parametrize("cfg", [TINY, SMALL, dict(N=4096, L=1, alpha=1)])
 def test_batching_is_slotwise(cfg):
     """decode is a ring map: products in Z_t[X]/(X^N+1) are slot-wise products."""
