@@ -74,7 +74,10 @@ typedef struct bfhe_ctx bfhe_ctx;
  * base of the exact multiply, K being the least count with B > 2 t N Q. */
 typedef struct {
     uint32_t N;          /* ring degree, power of two, 1024 .. 32768          */
-    uint32_t L;          /* data primes, 1 .. 16                               */
+    uint32_t L;          /* data primes, 1 .. 32; above 16 the base extensions */
+                         /* and the key-switch inner product run runtime-size */
+                         /* kernels (slower; meant for insecure, test-only    */
+                         /* moduli that hold deep circuits)                   */
     uint32_t alpha;      /* special primes, 1 or 2                             */
     uint32_t prime_bits; /* bit size of every modulus, 30 .. 58 (default 50)   */
     uint64_t t;          /* plaintext modulus: a prime = 1 (mod 2N), < 2^32,   */
@@ -84,8 +87,8 @@ typedef struct {
 
 /* The parameter rule alone, on the host (no device is touched): the moduli
  * a context with these parameters would use, in library order (data,
- * special, auxiliary; at least L + alpha + K entries in primes_out, 64 are
- * always enough), and K.  Same validation and errors as bfhe_ctx_create. */
+ * special, auxiliary; at least L + alpha + K entries in primes_out: 64 are
+ * enough up to 16 data primes, 80 always), and K.  Same validation and errors as bfhe_ctx_create. */
 int bfhe_param_primes(const bfhe_params* prm, uint64_t* primes_out, uint32_t* K_out);
 
 /* Create a context on CUDA device `device`.  Builds the moduli, NTT twiddles
@@ -94,7 +97,8 @@ int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** out);
 void bfhe_ctx_destroy(bfhe_ctx* ctx);
 
 /* Moduli in library order: primes_out[0 .. L+alpha+K-1] = q_0..q_{L-1},
- * p_0..p_{alpha-1}, b_0..b_{K-1} (host buffer of at least 64 entries);
+ * p_0..p_{alpha-1}, b_0..b_{K-1} (host buffer of at least L + alpha + K entries:
+ * 64 are enough up to 16 data primes, 80 always);
  * *K_out = K.  Also usable before keygen. */
 int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out);
 
@@ -113,13 +117,31 @@ int bfhe_reserve(bfhe_ctx* ctx, size_t n);
  * mixed-radix path when that sum is within 2n + 2 units of 1/2, where the
  * fixed-point rounding could pick the wrong v.  Results are identical
  * either way (bit for bit); only the speed differs.  Needs every modulus
- * below 2^50 (BFHE_EINVAL otherwise).  Default: on from 8 data primes up
- * (where it measured faster on GB300), off below.  bfhe_fast_extension
+ * below 2^50 and at most 16 data primes (BFHE_EINVAL otherwise).  Default: on
+ * from 8 to 16 data primes (where it measured faster on GB300), off
+ * otherwise.  bfhe_fast_extension
  * returns the current setting (1 or 0; BFHE_EINVAL for a NULL context).  The
  * paper has no counterpart: SEAL, which it runs on, uses approximate fast
  * conversions of this family. */
 int bfhe_set_fast_extension(bfhe_ctx* ctx, int on);
 int bfhe_fast_extension(const bfhe_ctx* ctx);
+
+/* mod_to_bits (and the two conversions inside mod_to_sint) runs its candidates
+ * c in tiles (Sec. 3.2.3, Eq. 2: one Fermat chain d_c^(t-1) per candidate,
+ * then the s products of Listing 8).  With graph tiles on, a call with at
+ * least two full tiles runs the first tile eagerly, captures the next one as
+ * a CUDA graph (its candidate base read from a context-owned device word)
+ * and replays that graph for every further full tile; the ragged last tile
+ * runs eagerly.  The work moves to a context-owned stream joined to the
+ * caller's stream by events, so the call stays asynchronous and ordered on
+ * the caller's stream.  The instantiated graph is kept for later calls with
+ * the same buffers and tile shape.  Results and op counts are identical
+ * either way; the first use allocates a word of device memory, a stream and
+ * two events.  With profiling on (bfhe_profile) tiles run eagerly.  Default:
+ * off.  bfhe_graph_tiles returns the setting (1 or 0; BFHE_EINVAL for a NULL
+ * context). */
+int bfhe_set_graph_tiles(bfhe_ctx* ctx, int on);
+int bfhe_graph_tiles(const bfhe_ctx* ctx);
 
 /* Process-wide device-memory budget for one call's scratch (default 16 GiB).
  * Calls whose batch needs more are tiled: the multiplies run in chunks that

@@ -12,7 +12,6 @@ Modules:
 - `workloads`: the genotype-shaped bridged job and the Fibonacci job.
 - `serving`: the continuous-batching request loop.
 - `autotune`: the NTT block-shape tuner.
-- `profile_cases`: small cases for profiling one kernel family.
 - `inputs`: the seeded synthetic input generators (no FHE arithmetic).
 - `build`: builds the library in-tree with nvcc for sm_103a.
 

@@ -75,6 +75,8 @@ def load():
         "bfhe_check": (I, [P, P, P]),
         "bfhe_set_fast_extension": (I, [P, I]),
         "bfhe_fast_extension": (I, [P]),
+        "bfhe_set_graph_tiles": (I, [P, I]),
+        "bfhe_graph_tiles": (I, [P]),
         "bfhe_scratch_budget": (S, []),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
@@ -115,7 +117,7 @@ class Context:
         torch.cuda.set_device(device)
         _check(self.lib.bfhe_ctx_create(ctypes.byref(prm), device, ctypes.byref(h)))
         self.h = h
-        buf = (ctypes.c_uint64 * 64)()
+        buf = (ctypes.c_uint64 * 80)()
         K = ctypes.c_uint32()
         _check(self.lib.bfhe_ctx_primes(self.h, buf, ctypes.byref(K)))
         self.K = K.value
@@ -166,6 +168,17 @@ class Context:
     @property
     def fast_extension(self):
         rc = self.lib.bfhe_fast_extension(self.h)
+        if rc < 0:
+            _check(rc)
+        return bool(rc)
+
+    def set_graph_tiles(self, on):
+        """mod_to_bits replays its full candidate tiles from one captured CUDA graph (same results)."""
+        _check(self.lib.bfhe_set_graph_tiles(self.h, int(bool(on))))
+
+    @property
+    def graph_tiles(self):
+        rc = self.lib.bfhe_graph_tiles(self.h)
         if rc < 0:
             _check(rc)
         return bool(rc)
@@ -385,7 +398,7 @@ def param_primes(N, L, alpha, t=65537, prime_bits=50):
     """Moduli (data, special, auxiliary) and K of the parameter rule, computed on the host."""
     lib = load()
     prm = _Params(N, L, alpha, prime_bits, t)
-    buf = (ctypes.c_uint64 * 64)()
+    buf = (ctypes.c_uint64 * 80)()
     K = ctypes.c_uint32(0)
     _check(lib.bfhe_param_primes(ctypes.byref(prm), buf, ctypes.byref(K)))
     return [int(buf[i]) for i in range(L + alpha + K.value)], K.value

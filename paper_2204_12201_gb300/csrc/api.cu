@@ -31,13 +31,6 @@ size_t g_scratch_budget = (size_t)16 << 30;
 
 size_t mul_words_per_ct(const bfhe_ctx* c) { return mul_scratch_bytes(c, 1) / sizeof(u64); }
 
-// largest tile of ciphertexts whose multiply scratch fits in `bytes`
-size_t mul_tile(const bfhe_ctx* c, size_t bytes) {
-    size_t per = mul_scratch_bytes(c, 1);
-    size_t t = bytes / per;
-    return t ? t : 1;
-}
-
 // out[i] = a[i] * b[i] (relinearised), n ciphertexts, scratch of `scratch_words` words
 int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, u64* scratch,
                    size_t scratch_words, cudaStream_t st) {
@@ -75,7 +68,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         io3.in_os = io3.out_os = 4 * LK * N;
         io3.in_is = io3.out_is = LK * N;
         io3.in_ls = io3.out_ls = N;
-        RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st, 1));   // scale takes words < 2q
+        RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st, 2));   // scale applies the twist
         RC(launch_scale(c, X, C3, m, st));
         NttIO iod;   // digit j of c2 (limb j of C3 slot 2), reduced into every prime of Q u P
         iod.in = C3 + 2 * L * N;
@@ -89,7 +82,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         iod.out_ls = N;
         RC(launch_ntt_fwd(c, iod, m * (int)L, (int)QP, c->mapQP(), st, 1));   // so does the inner product
         RC(launch_inner(c, Dg, W, m, st));
-        RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st, 1));   // so does mod-down
+        RC(launch_ntt_inv(c, ntt_io(W, W, QP, N), 2 * m, (int)QP, c->mapQP(), 1, st, 2));   // so does mod-down
         RC(launch_moddown(c, W, C3, o, m, st));
     }
     return BFHE_OK;
@@ -185,8 +178,21 @@ extern "C" int bfhe_set_fast_extension(bfhe_ctx* c, int on) {
     CHECK_CTX(c);
     if (on && !(c->ext_QB.fast_ok && c->ext_BQ.fast_ok))
         return set_error(BFHE_EINVAL, "the fast extension needs every modulus below 2^50");
+    if (on && c->L > BFHE_MAX_L_UNROLLED)
+        return set_error(BFHE_EINVAL, "the fast extension is built for at most 16 data primes");
     c->fast_ext = on != 0;
     return BFHE_OK;
+}
+
+extern "C" int bfhe_set_graph_tiles(bfhe_ctx* c, int on) {
+    CHECK_CTX(c);
+    c->graph_tiles = on != 0;
+    return BFHE_OK;
+}
+
+extern "C" int bfhe_graph_tiles(const bfhe_ctx* c) {
+    if (!c) return set_error(BFHE_EINVAL, "null context");
+    return c->graph_tiles ? 1 : 0;
 }
 
 extern "C" int bfhe_fast_extension(const bfhe_ctx* c) {
@@ -607,12 +613,89 @@ bool m2b_args_ok(const bfhe_ctx* c, uint32_t s, u64 c_lo, u64 c_hi, int mode) {
     return s != 0 && s <= 63 && c_hi >= c_lo && c_hi < c->t && (mode == BFHE_PAPER || mode == BFHE_SELECT);
 }
 
+// One tile of Ct candidates c_base .. c_base + Ct - 1 (Eq. 2, Listings 7-8): d_c = x - c, eq_c = 1 - d_c^(t-1),
+// then PAPER: s products of eq_c with the trivially encrypted bits of c, summed into the bits; SELECT: eq_c
+// added to bit k when bit k of c is 1.  cbp, when not null, is a device word holding c_base (graph replay).
+int m2b_tile(bfhe_ctx* c, const u64* x, uint32_t s, u64 c_base, const u64* cbp, int Ct, int mode, u64* bits_out,
+             size_t n, u64* fixed, u64* mul, size_t mw, cudaStream_t st) {
+    const size_t ctw = c->ct_words();
+    const u64 e = c->t - 1;
+    const size_t m = (size_t)Ct * n;   // chains in this tile
+    u64* D = fixed;                     // [Ct][n]
+    u64* bufs = D + m * ctw;            // pow buffers
+    u64* EQ = bufs + pow_buf_words(c, e, m);
+    RC(launch_sub_const_chains(c, x, D, c_base, cbp, Ct, n, st));
+    c->counts[1] += m;
+    RC(pow_impl(c, D, e, EQ, m, bufs, mul, mw, st));
+    RC(launch_lincomb(c, EQ, EQ, nullptr, nullptr, nullptr, LinCoef{1, -1, 0, 0, 0}, 1, m, st));
+    c->counts[1] += m;
+    if (mode == BFHE_PAPER) {
+        u64* TR = EQ + m * ctw;              // [s][Ct][n] trivial bits
+        u64* RP = TR + (size_t)s * m * ctw;  // [s][Ct][n] copies of eq
+        u64* PR = RP + (size_t)s * m * ctw;  // products
+        RC(launch_trivial_bits(c, TR, s, c_base, cbp, Ct, n, st));
+        for (uint32_t k = 0; k < s; ++k)
+            BFHE_CUDA(cudaMemcpyAsync(RP + (size_t)k * m * ctw, EQ, m * ctw * sizeof(u64), cudaMemcpyDeviceToDevice,
+                                      st));
+        RC(mul_relin_impl(c, TR, RP, PR, (size_t)s * m, mul, mw, st));
+        c->counts[2] += (uint64_t)s * m;
+        RC(launch_accumulate(c, bits_out, PR, s, c_base, cbp, Ct, n, 0, st));
+    } else {
+        RC(launch_accumulate(c, bits_out, EQ, s, c_base, cbp, Ct, n, 1, st));
+    }
+    return BFHE_OK;
+}
+
+// Captures one full tile on the context's capture stream (candidate base read from c->d_cbase) and keeps the
+// instantiated graph with its key; records the op counts and kernel launches of one tile.
+int m2b_capture(bfhe_ctx* c, const std::vector<u64>& key, const u64* x, uint32_t s, int C, int mode, u64* bits_out,
+                size_t n, u64* fixed, u64* mul, size_t mw) {
+    cudaStream_t cs = c->cap_stream;
+    if (c->tile_exec) {
+        BFHE_CUDA(cudaStreamSynchronize(cs));   // the old graph may still be running
+        cudaGraphExecDestroy(c->tile_exec);
+        c->tile_exec = nullptr;
+        c->tile_key.clear();
+    }
+    uint64_t counts0[4];
+    for (int k = 0; k < 4; ++k) counts0[k] = c->counts[k];
+    const uint64_t l0 = bfhe_launch_count();
+    BFHE_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    const int rc = m2b_tile(c, x, s, 0, c->d_cbase, C, mode, bits_out, n, fixed, mul, mw, cs);
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (rc != BFHE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ec != cudaSuccess) return cuda_check(ec, "cudaStreamEndCapture (mod_to_bits tile)");
+    const cudaError_t ei = cudaGraphInstantiate(&c->tile_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->tile_exec = nullptr;
+        return cuda_check(ei, "cudaGraphInstantiate (mod_to_bits tile)");
+    }
+    // the capture recorded the tile without running it: its counts are those of one tile
+    for (int k = 0; k < 4; ++k) {
+        c->tile_counts[k] = c->counts[k] - counts0[k];
+        c->counts[k] = counts0[k];
+    }
+    c->tile_launches = bfhe_launch_count() - l0;
+    count_launches((uint64_t)0 - c->tile_launches);
+    c->tile_key = key;
+    return BFHE_OK;
+}
+
 // Sec. 3.2.3, Eq. 2, Listings 7-8; the first `reserve` words of the arena are left to the caller
 // (the arena must already hold them if they carry data: it is grown only when it is too small).
+// With graph tiles on and at least two full tiles, the first tile runs eagerly and the other full tiles
+// replay one captured tile, all on the context's capture stream (joined to `st` by events); the ragged
+// last tile runs eagerly.
 int mod_to_bits_impl(bfhe_ctx* c, const u64* x, uint32_t s, u64 c_lo, u64 c_hi, int mode, u64* bits_out,
                      size_t n, size_t reserve, cudaStream_t st) {
     const size_t ctw = c->ct_words();
-    const u64 e = c->t - 1;
     const size_t total = c_hi - c_lo + 1;
     const M2BPlan pl = m2b_plan(c, s, total, mode, n, reserve);
     const size_t C = pl.C;
@@ -620,41 +703,50 @@ int mod_to_bits_impl(bfhe_ctx* c, const u64* x, uint32_t s, u64 c_lo, u64 c_hi, 
     size_t mw;
     RC(scratch_for(c, pl.fixed_words, pl.n_mul, &fixed, &mul, &mw));
     fixed += reserve;
-    BFHE_CUDA(cudaMemsetAsync(bits_out, 0, (size_t)s * n * ctw * sizeof(u64), st));
-    std::vector<size_t> terms(s, 0);
+    const size_t full = total / C;
+    const bool graph = c->graph_tiles && full >= 2 && !c->prof_on;
+    cudaStream_t ws = st;
+    if (graph) {
+        if (!c->cap_stream) BFHE_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (!c->cap_in) BFHE_CUDA(cudaEventCreateWithFlags(&c->cap_in, cudaEventDisableTiming));
+        if (!c->cap_out) BFHE_CUDA(cudaEventCreateWithFlags(&c->cap_out, cudaEventDisableTiming));
+        if (!c->d_cbase) BFHE_CUDA(cudaMalloc(&c->d_cbase, sizeof(u64)));
+        BFHE_CUDA(cudaEventRecord(c->cap_in, st));
+        BFHE_CUDA(cudaStreamWaitEvent(c->cap_stream, c->cap_in, 0));
+        ws = c->cap_stream;
+    }
+    BFHE_CUDA(cudaMemsetAsync(bits_out, 0, (size_t)s * n * ctw * sizeof(u64), ws));
     for (size_t cb = 0; cb < total; cb += C) {
         const int Ct = (int)std::min(C, total - cb);
         const u64 c_base = c_lo + cb;
-        const size_t m = (size_t)Ct * n;   // chains in this tile
-        u64* D = fixed;                     // [Ct][n]
-        u64* bufs = D + m * ctw;            // pow buffers
-        u64* EQ = bufs + pow_buf_words(c, e, m);
-        RC(launch_sub_const_chains(c, x, D, c_base, Ct, n, st));
-        c->counts[1] += m;
-        RC(pow_impl(c, D, e, EQ, m, bufs, mul, mw, st));
-        RC(launch_lincomb(c, EQ, EQ, nullptr, nullptr, nullptr, LinCoef{1, -1, 0, 0, 0}, 1, m, st));
-        c->counts[1] += m;
-        if (mode == BFHE_PAPER) {
-            u64* TR = EQ + m * ctw;              // [s][Ct][n] trivial bits
-            u64* RP = TR + (size_t)s * m * ctw;  // [s][Ct][n] copies of eq
-            u64* PR = RP + (size_t)s * m * ctw;  // products
-            RC(launch_trivial_bits(c, TR, s, c_base, Ct, n, st));
-            for (uint32_t k = 0; k < s; ++k)
-                BFHE_CUDA(cudaMemcpyAsync(RP + (size_t)k * m * ctw, EQ, m * ctw * sizeof(u64),
-                                          cudaMemcpyDeviceToDevice, st));
-            RC(mul_relin_impl(c, TR, RP, PR, (size_t)s * m, mul, mw, st));
-            c->counts[2] += (uint64_t)s * m;
-            RC(launch_accumulate(c, bits_out, PR, s, c_base, Ct, n, 0, st));
-            for (uint32_t k = 0; k < s; ++k) terms[k] += Ct;
+        if (graph && cb > 0 && (size_t)Ct == C) {
+            const std::vector<u64> key = {(u64)(uintptr_t)x, (u64)(uintptr_t)bits_out, (u64)(uintptr_t)fixed,
+                                          (u64)(uintptr_t)mul, mw, n, s, C, (u64)mode, c->fast_ext ? 1ull : 0ull};
+            if (!c->tile_exec || c->tile_key != key)
+                RC(m2b_capture(c, key, x, s, (int)C, mode, bits_out, n, fixed, mul, mw));
+            RC(launch_set_word(c->d_cbase, c_base, ws));
+            BFHE_CUDA(cudaGraphLaunch(c->tile_exec, ws));
+            for (int k = 0; k < 4; ++k) c->counts[k] += c->tile_counts[k];
+            count_launches(c->tile_launches);
         } else {
-            RC(launch_accumulate(c, bits_out, EQ, s, c_base, Ct, n, 1, st));
-            for (uint32_t k = 0; k < s; ++k)
-                for (int j = 0; j < Ct; ++j)
-                    if (((c_base + j) >> k) & 1) terms[k] += 1;
+            RC(m2b_tile(c, x, s, c_base, nullptr, Ct, mode, bits_out, n, fixed, mul, mw, ws));
         }
     }
-    for (uint32_t k = 0; k < s; ++k)
-        if (terms[k] > 1) c->counts[0] += (uint64_t)(terms[k] - 1) * n;
+    if (graph) {
+        BFHE_CUDA(cudaEventRecord(c->cap_out, ws));
+        BFHE_CUDA(cudaStreamWaitEvent(st, c->cap_out, 0));
+    }
+    // the paper's accounting of the final sums: one addition per term after the first, per bit
+    for (uint32_t k = 0; k < s; ++k) {
+        size_t terms = 0;
+        if (mode == BFHE_PAPER) {
+            terms = total;
+        } else {
+            for (size_t j = 0; j < total; ++j)
+                if (((c_lo + j) >> k) & 1) terms += 1;
+        }
+        if (terms > 1) c->counts[0] += (uint64_t)(terms - 1) * n;
+    }
     return BFHE_OK;
 }
 

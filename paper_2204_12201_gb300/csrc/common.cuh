@@ -19,9 +19,12 @@ typedef uint64_t u64;
 typedef int64_t i64;
 typedef unsigned __int128 u128;
 
-#define BFHE_MAX_L 16
+// up to 16 data primes every kernel has a compiled instance per size; 17..32 (insecure, test-only
+// parameter sets for deep circuits) run runtime-size variants of the base extensions and the inner product
+#define BFHE_MAX_L 32
+#define BFHE_MAX_L_UNROLLED 16
 #define BFHE_MAX_ALPHA 2
-#define BFHE_MAX_PRIMES 64
+#define BFHE_MAX_PRIMES 80
 #define BFHE_MAX_DEVICES 64
 
 // ------------------------------------------------------------------ device modular arithmetic
@@ -53,6 +56,21 @@ __host__ __device__ __forceinline__ u64 shoup_lazy4(u64 a, u64 w, u64 ws, u64 q)
     const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), w0 = (uint32_t)ws, w1 = (uint32_t)(ws >> 32);
     const u64 hi = (u64)a1 * w1 + (((u64)a1 * w0) >> 32) + (((u64)a0 * w1) >> 32);
     return a * w - hi * q;
+}
+
+// The same product with the modulus passed negated (nq = 2^64 - q): r = a w + h nq mod 2^64, written
+// in 32-bit pieces so that each partial product is one multiply-add (the low word of a0 w0 + h0 nq0 as
+// one wide multiply-add, the high word as four narrow ones).
+__device__ __forceinline__ u64 shoup_lazy4n(u64 a, u64 w, u64 ws, u64 nq) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), s0 = (uint32_t)ws, s1 = (uint32_t)(ws >> 32);
+    u64 h = (u64)a1 * s1 + __umulhi(a1, s0);
+    h += __umulhi(a0, s1);
+    const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
+    const uint32_t w0 = (uint32_t)w, w1 = (uint32_t)(w >> 32), n0 = (uint32_t)nq, n1 = (uint32_t)(nq >> 32);
+    u64 r = (u64)a0 * w0;
+    r += (u64)h0 * n0;
+    const uint32_t rh = (uint32_t)(r >> 32) + a0 * w1 + a1 * w0 + h0 * n1 + h1 * n0;
+    return ((u64)rh << 32) | (uint32_t)r;
 }
 
 __host__ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
@@ -120,7 +138,7 @@ struct PrimeTab {
     const u64* mu;       // floor(2^64 / q)
     const u64* tw;       // [nP][N][2] (psi^brv(k), Shoup companion)      forward twiddles
     const u64* itw;      // [nP][N][2] inverse (DIT) twiddles: entry 2^b + j = omega^-(N/2^(b+1)) j, omega = psi^2
-    const u64* twist;    // [nP][2][N][2] output twist N^-1 psi^-m (plain; times 2^64 mod q)
+    const u64* twist;    // [nP][3][N][2] output twist N^-1 psi^-m (plain; times R = 2^64; times t R), mod q
 };
 
 // limb -> prime index map of a polynomial base: limb < split ? limb : limb + off
@@ -171,6 +189,19 @@ struct bfhe_ctx {
     uint64_t counts[4] = {0, 0, 0, 0};
     bool fast_ext = false;       // guarded fast base extension in the multiply (bfhe_set_fast_extension)
 
+    // mod_to_bits tiles replayed from a CUDA graph (bfhe_set_graph_tiles): the tile is captured once on a
+    // context-owned stream and replayed with its candidate base in the device word d_cbase; the
+    // instantiated graph is kept for later calls with the same buffers and shape (key)
+    bool graph_tiles = false;
+    bool capturing = false;      // inside a stream capture: no profiling events
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t cap_in = nullptr, cap_out = nullptr;
+    u64* d_cbase = nullptr;
+    cudaGraphExec_t tile_exec = nullptr;
+    std::vector<u64> tile_key;
+    uint64_t tile_counts[4] = {0, 0, 0, 0};   // op counts of one captured tile
+    uint64_t tile_launches = 0;                // kernels in the captured tile
+
     // launch timing (measurement only): pending (class, start, stop) event triples
     struct ProfRec {
         int cls;
@@ -192,6 +223,7 @@ struct bfhe_ctx {
 int set_error(int code, const std::string& msg);
 // process-wide count of kernel launches made by this library (measurement)
 void count_launch();
+void count_launches(uint64_t n);   // kernels launched by a graph replay
 int cuda_check(cudaError_t e, const char* where);
 #define BFHE_CUDA(call)                                          \
     do {                                                         \
@@ -249,8 +281,9 @@ inline NttIO ntt_io(const u64* in, u64* out, size_t n_limbs, size_t N) {
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
                    int lazy_out = 0);
 // mont != 0: the final scale is N^-1 R (undoes one Montgomery factor R^-1 of the inputs)
-// lazy_out: outputs below 2q (the twist product without its final subtraction) for consumers that
-// take lazy words (scale-and-round, mod-down); otherwise canonical
+// lazy_out: 0 canonical; 1 outputs below 2q (the twist product without its final subtraction) for consumers
+// that take lazy words; 2 no twist at all (words below 61q, from inputs below q) for consumers that fold the
+// twist into a product of their own (scale-and-round, mod-down)
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
                    cudaStream_t st, int lazy_out = 0);
 int ntt_config(int logN, int inverse, int* log_m, int* log_e);

@@ -168,9 +168,16 @@ __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, in
     }
 }
 
-// scale-and-round of the tensor (X slots 0..2, Q u B limbs) into C3 [n][3][L][N]
+// pair (w, Shoup(w)) of the twist table row f of prime p at coefficient k: f = 1 is N^-1 psi^-k R,
+// f = 2 is t N^-1 psi^-k R (mod the prime)
+__device__ __forceinline__ ulonglong2 twist_at(const u64* twist, int p, int f, int k, int N) {
+    return __ldg(reinterpret_cast<const ulonglong2*>(twist) + ((size_t)p * 3 + f) * N + k);
+}
+
+// scale-and-round of the tensor (X slots 0..2, Q u B limbs) into C3 [n][3][L][N].  The inverse transforms
+// leave the tensor untwisted: the first product of each limb, by t, also carries the twist N^-1 psi^-k R.
 template <int NS, int KS, bool FAST>
-__global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* tmod, int nP,
+__global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* twist, int nP,
                         const u64* Qinv_b, const u64* bq, int N) {
     const size_t total = (size_t)n * 3 * N;
     constexpr int LK = NS + KS;
@@ -185,7 +192,8 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const u64 qi = eQB.src_q[i];
-            r[i] = shoup_lazy(d[(size_t)i * N], tmod[i], tmod[nP + i], qi);   // [t d]_{q_i}, < 2 q_i
+            const ulonglong2 f = twist_at(twist, i, 2, k, N);
+            r[i] = shoup_lazy(d[(size_t)i * N], f.x, f.y, qi);   // [t d]_{q_i}, < 2 q_i
         }
         // r -> B (centred), then y = (t d - r) / Q in B
         u64 y[KS];
@@ -201,7 +209,8 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
             for (int j = 0; j < KS; ++j) {
                 const u64 bj = bq[j];
                 const int pj = NS + (nP - 1 - NS - KS) + j;                      // prime index of b_j
-                const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], tmod[pj], tmod[nP + pj], bj);   // < 2 b_j
+                const ulonglong2 f = twist_at(twist, pj, 2, k, N);
+                const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], f.x, f.y, bj);   // [t d]_{b_j}, < 2 b_j
                 u64 rb;
                 if constexpr (FAST) rb = fast ? fast_eval<NS>(r0, r1, vv, eQB, j) : ext_eval<NS, false>(v, neg, eQB, j);
                 else rb = ext_eval<NS, false>(v, neg, eQB, j);
@@ -226,10 +235,11 @@ __global__ void k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, 
     }
 }
 
-// out[c][comp] = C3[c][comp] + round(W / P) mod Q, W over Q u P (coefficient form)
+// out[c][comp] = C3[c][comp] + round(W / P) mod Q, W over Q u P (coefficient form, untwisted: each word is
+// first multiplied by the twist N^-1 psi^-k R that the inverse transform left out)
 template <int NA>
 __global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, ExtDesc ePQ, const u64* Pinv,
-                          const u64* qtab, int N) {
+                          const u64* qtab, const u64* twist, int N) {
     const size_t total = (size_t)n * 2 * N;
     const int QP = L + NA;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -241,14 +251,19 @@ __global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, E
         const u64* w = W + cp * (size_t)QP * N + k;
         u64 x[NA], v[NA];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) x[a] = w[(size_t)(L + a) * N];
+        for (int a = 0; a < NA; ++a) {
+            const ulonglong2 f = twist_at(twist, L + a, 1, k, N);
+            x[a] = shoup_lazy(w[(size_t)(L + a) * N], f.x, f.y, ePQ.src_q[a]);   // < 2 p_a
+        }
         const bool neg = garner<NA>(x, ePQ, v);
         const u64* cin = C3 + (c * 3 + comp) * (size_t)L * N + k;
         u64* o = out + cp * (size_t)L * N + k;
         for (int i = 0; i < L; ++i) {
             const u64 qi = qtab[i];
+            const ulonglong2 f = twist_at(twist, i, 1, k, N);
+            const u64 wi = shoup_lazy(w[(size_t)i * N], f.x, f.y, qi);   // < 2 q_i
             const u64 e = ext_eval<NA, false>(v, neg, ePQ, i);
-            const u64 y = shoup(sub_mod(w[(size_t)i * N], e, qi), Pinv[i], Pinv[L + i], qi);
+            const u64 y = shoup(sub_mod(wi, e, qi), Pinv[i], Pinv[L + i], qi);
             o[(size_t)i * N] = add_mod(cin[(size_t)i * N], y, qi);
         }
     }
@@ -280,6 +295,137 @@ __global__ void k_dec_finish(const u64* V, const u64* ct, u64* M, int n, ExtDesc
     }
 }
 
+// ---------------------------------------------------------------- more than 16 data primes
+// The insecure test-only parameter sets with 17..BFHE_MAX_L data primes run the same exact arithmetic with
+// sizes known only at run time (digits in local memory, loops not unrolled), so that they need no template
+// instance per size; the guarded fast extension is not offered there.
+constexpr int NMAX = BFHE_MAX_L + 1;
+
+__device__ bool garner_n(const u64* x, const ExtDesc& d, u64* v, int ns) {
+#pragma unroll 1
+    for (int i = 0; i < ns; ++i) {
+        const u64 si = d.src_q[i];
+        u64 u = x[i];
+#pragma unroll 1
+        for (int j = 0; j < i; ++j) {
+            u64 vj = v[j];
+            vj = vj >= si ? vj - si : vj;
+            u = shoup_lazy(u + si - vj, d.ginv[i * ns + j], d.ginv_s[i * ns + j], si);
+        }
+        v[i] = u >= si ? u - si : u;
+    }
+    int state = 0;
+#pragma unroll 1
+    for (int i = ns - 1; i >= 0 && state == 0; --i) {
+        const u64 h = d.hdig[i];
+        state = v[i] > h ? 1 : (v[i] < h ? -1 : 0);
+    }
+    return state > 0;
+}
+
+__device__ u64 ext_eval_n(const u64* v, bool neg, const ExtDesc& d, int j, int ns, bool small) {
+    const u64 T = d.dst_q[j];
+    u64 acc;
+    if (small) {
+        const u64 mu = d.dst_mu[j];
+        acc = reduce64(v[ns - 1], T, mu);
+#pragma unroll 1
+        for (int i = ns - 2; i >= 0; --i) {
+            acc = shoup(acc, d.radix[j * ns + i], d.radix_s[j * ns + i], T);
+            acc = add_mod(acc, reduce64(v[i], T, mu), T);
+        }
+    } else {
+        acc = v[ns - 1];
+#pragma unroll 1
+        for (int i = ns - 2; i >= 0; --i) acc = shoup_lazy(acc, d.radix[j * ns + i], d.radix_s[j * ns + i], T) + v[i];
+        const u64 T2 = T << 1;
+        acc = acc >= T2 ? acc - T2 : acc;
+        acc = acc >= T ? acc - T : acc;
+    }
+    if (neg) acc = sub_mod(acc, d.smod[j], T);
+    return acc;
+}
+
+__global__ void k_modup_n(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
+                          uint32_t* flags) {
+    const int ns = ext.n_src;
+    const size_t total = (size_t)n * slots * N;
+    const int LK = ns + K;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t pp = idx / N;
+        const size_t c = pp / slots;
+        const int slot = (int)(pp % slots);
+        const u64* src = (slot < 2 ? A : B) + (c * 2 + (slot & 1)) * (size_t)ns * N + k;
+        u64* dst = X + (c * 4 + slot) * (size_t)LK * N + k;
+        u64 x[NMAX], v[NMAX];
+        bool bad = false;
+        for (int i = 0; i < ns; ++i) {
+            x[i] = src[(size_t)i * N];
+            dst[(size_t)i * N] = x[i];
+            bad |= x[i] >= ext.src_q[i];
+        }
+        if (bad) atomicOr(flags, BFHE_FLAG_RESIDUE);
+        const bool neg = garner_n(x, ext, v, ns);
+        for (int j = 0; j < K; ++j) dst[(size_t)(ns + j) * N] = ext_eval_n(v, neg, ext, j, ns, false);
+    }
+}
+
+__global__ void k_scale_n(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* twist, int nP,
+                          const u64* Qinv_b, const u64* bq, int N) {
+    const int ns = eQB.n_src, ks = eBQ.n_src, LK = ns + ks;
+    const size_t total = (size_t)n * 3 * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t cp = idx / N;
+        const size_t c = cp / 3;
+        const int comp = (int)(cp % 3);
+        const u64* d = X + (c * 4 + comp) * (size_t)LK * N + k;
+        u64 r[NMAX], v[NMAX], y[NMAX];
+        for (int i = 0; i < ns; ++i) {
+            const ulonglong2 f = twist_at(twist, i, 2, k, N);
+            r[i] = shoup_lazy(d[(size_t)i * N], f.x, f.y, eQB.src_q[i]);
+        }
+        const bool neg = garner_n(r, eQB, v, ns);
+        for (int j = 0; j < ks; ++j) {
+            const u64 bj = bq[j];
+            const int pj = ns + (nP - 1 - ns - ks) + j;
+            const ulonglong2 f = twist_at(twist, pj, 2, k, N);
+            const u64 td = shoup_lazy(d[(size_t)(ns + j) * N], f.x, f.y, bj);
+            const u64 rb = ext_eval_n(v, neg, eQB, j, ns, false);
+            y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[ks + j], bj);
+        }
+        const bool negy = garner_n(y, eBQ, v, ks);
+        u64* o = C3 + cp * (size_t)ns * N + k;
+        for (int i = 0; i < ns; ++i) o[(size_t)i * N] = ext_eval_n(v, negy, eBQ, i, ks, false);
+    }
+}
+
+__global__ void k_dec_finish_n(const u64* V, const u64* ct, u64* M, int n, ExtDesc eQt, const u64* tmod, int nP,
+                               u64 Qinv_t, int N, uint32_t* flags) {
+    const int ns = eQt.n_src;
+    const size_t total = (size_t)n * N;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const size_t c = idx / N;
+        u64 r[NMAX], v[NMAX];
+        for (int i = 0; i < ns; ++i) {
+            const u64 qi = eQt.src_q[i];
+            const u64 c0 = ct[(c * 2 * ns + i) * N + k];
+            if (c0 >= qi) atomicOr(flags, BFHE_FLAG_RESIDUE);
+            r[i] = shoup(add_mod(V[(c * ns + i) * N + k], c0, qi), tmod[i], tmod[nP + i], qi);
+        }
+        const bool neg = garner_n(r, eQt, v, ns);
+        const u64 t = eQt.dst_q[0];
+        const u64 rho = ext_eval_n(v, neg, eQt, 0, ns, true);
+        const u64 mneg = rho == 0 ? 0 : t - rho;
+        M[idx] = (mneg * Qinv_t) % t;
+    }
+}
+
 }  // namespace
 
 // ================================================================== launchers
@@ -305,10 +451,10 @@ int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st
     const size_t work = (size_t)n * 3 * ctx->N;
     const u64* bq = ctx->tab.q + ctx->L + ctx->alpha;
     if (ctx->fast_ext && ctx->ext_QB.fast_ok && ctx->ext_BQ.fast_ok)
-        LAUNCH((k_scale<NS, NS + 1, true>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
+        LAUNCH((k_scale<NS, NS + 1, true>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
                ctx->d_Qinv_b, bq, (int)ctx->N);
     else
-        LAUNCH((k_scale<NS, NS + 1, false>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->d_tmod, (int)ctx->nP,
+        LAUNCH((k_scale<NS, NS + 1, false>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
                ctx->d_Qinv_b, bq, (int)ctx->N);
     return BFHE_OK;
 }
@@ -339,13 +485,17 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
         case 14: return FN<14>(__VA_ARGS__);                                                                   \
         case 15: return FN<15>(__VA_ARGS__);                                                                   \
         case 16: return FN<16>(__VA_ARGS__);                                                                   \
-        default: return set_error(BFHE_EINVAL, "unsupported number of data primes");                         \
+        default: break;                                                                                        \
     }
 
 int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const double L_ = ctx->L, K_ = ctx->K;
     ProfScope ps(ctx, BFHE_K_MODUP, st, (double)slots * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
     SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, slots, st)
+    if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
+    LAUNCH(k_modup_n, (size_t)n * slots * ctx->N, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N,
+           ctx->d_flags);
+    return BFHE_OK;
 }
 
 int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st) {
@@ -354,16 +504,23 @@ int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t
     ProfScope ps(ctx, BFHE_K_SCALE, st,
                  3.0 * n * ctx->N * (2 * L_ + 3 * K_ + L_ * (L_ - 1) / 2 + K_ * (L_ - 1) + K_ * (K_ - 1) / 2 + L_ * (K_ - 1)));
     SWITCH_L(ctx->L, run_scale, ctx, X, C3, n, st)
+    if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
+    LAUNCH(k_scale_n, (size_t)n * 3 * ctx->N, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
+           ctx->d_Qinv_b, ctx->tab.q + ctx->L + ctx->alpha, (int)ctx->N);
+    return BFHE_OK;
 }
 
 int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st) {
     const double A_ = ctx->alpha;
-    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_));
+    // work: the rounding division by P, plus the twist the inverse transform left to this kernel
+    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_ + ctx->L + A_));
     const size_t work = (size_t)n * 2 * ctx->N;
     if (ctx->alpha == 1)
-        LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
+        LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, ctx->tab.twist,
+               (int)ctx->N);
     else if (ctx->alpha == 2)
-        LAUNCH(k_moddown<2>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, (int)ctx->N);
+        LAUNCH(k_moddown<2>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, ctx->tab.twist,
+               (int)ctx->N);
     else
         return set_error(BFHE_EINVAL, "alpha must be 1 or 2");
     return BFHE_OK;
@@ -371,5 +528,9 @@ int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, i
 
 int launch_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int n, cudaStream_t st) {
     SWITCH_L(ctx->L, run_dec_finish, ctx, V, ct, M, n, st)
+    if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
+    LAUNCH(k_dec_finish_n, (size_t)n * ctx->N, V, ct, M, n, ctx->ext_Qt, ctx->d_tmod, (int)ctx->nP, ctx->Qinv_t,
+           (int)ctx->N, ctx->d_flags);
+    return BFHE_OK;
 }
 

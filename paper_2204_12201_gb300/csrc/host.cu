@@ -256,6 +256,7 @@ std::vector<u64> pair_table(const std::vector<u64>& w, const std::vector<u64>& q
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 extern "C" uint64_t bfhe_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -297,7 +298,7 @@ static cudaEvent_t take_event(const bfhe_ctx* c) {
 }
 
 ProfScope::ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w) : c(ctx), cls(k), work(w), st(s) {
-    if (!c->prof_on) return;
+    if (!c->prof_on || c->capturing) return;
     a = take_event(c);
     b = take_event(c);
     if (a && b) cudaEventRecord(a, st);
@@ -380,7 +381,7 @@ static int param_rule(const bfhe_params* prm, ParamRule* r) {
     if (!prm) return set_error(BFHE_EINVAL, "null argument");
     const uint32_t N = prm->N;
     if (N < 1024 || N > 32768 || (N & (N - 1))) return set_error(BFHE_EINVAL, "N must be a power of two in [1024, 32768]");
-    if (prm->L < 1 || prm->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "L must be in [1, 16]");
+    if (prm->L < 1 || prm->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "L must be in [1, 32]");
     if (prm->alpha < 1 || prm->alpha > BFHE_MAX_ALPHA) return set_error(BFHE_EINVAL, "alpha must be 1 or 2");
     const uint32_t bits = prm->prime_bits ? prm->prime_bits : 50;
     if (bits < 30 || bits > 58) return set_error(BFHE_EINVAL, "prime_bits must be in [30, 58]");   // NTT bound 64q <= 2^64
@@ -491,7 +492,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     // per-prime tables
     Arena ar;
     std::vector<u64> qv(c->primes), qinv(nP), mu(nP), R2(nP);
-    std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2), twist((size_t)nP * 2 * N * 2);
+    std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2), twist((size_t)nP * 3 * N * 2);
     for (uint32_t p = 0; p < nP; ++p) {
         const u64 q = c->primes[p];
         if (p == nP - 1 && !batching) {
@@ -531,15 +532,17 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
                 itw[o + 1] = shoup_of(itw[o], q);
             }
         }
-        // twist N^-1 psi^-m, plain and times R
-        const u64 ninv = invmod(N % q, q);
+        // twist N^-1 psi^-m: plain, times R, and times t R (scale-and-round takes the multiply's inverse
+        // transforms untwisted and folds the twist into its own product by t)
+        const u64 ninv = invmod(N % q, q), tq = t % q;
         for (uint32_t m = 0; m < N; ++m) {
-            const u64 v0 = mulmod(ninv, ipw[m], q), v1 = mulmod(v0, R, q);
-            const size_t o0 = (((size_t)p * 2 + 0) * N + m) * 2, o1 = (((size_t)p * 2 + 1) * N + m) * 2;
-            twist[o0] = v0;
-            twist[o0 + 1] = shoup_of(v0, q);
-            twist[o1] = v1;
-            twist[o1 + 1] = shoup_of(v1, q);
+            const u64 v0 = mulmod(ninv, ipw[m], q), v1 = mulmod(v0, R, q), v2 = mulmod(v1, tq, q);
+            const u64 vs[3] = {v0, v1, v2};
+            for (int f = 0; f < 3; ++f) {
+                const size_t o = (((size_t)p * 3 + f) * N + m) * 2;
+                twist[o] = vs[f];
+                twist[o + 1] = shoup_of(vs[f], q);
+            }
         }
     }
     const size_t o_q = ar.add(qv), o_qinv = ar.add(qinv), o_mu = ar.add(mu), o_R2 = ar.add(R2);
@@ -616,7 +619,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->ext_PQ = ext_ptrs(base, ePQ);
     c->ext_Qt = ext_ptrs(base, eQt);
     // the guarded fast extension measures faster from 8 data primes up (slower at 2)
-    c->fast_ext = c->L >= 8 && c->ext_QB.fast_ok && c->ext_BQ.fast_ok;
+    c->fast_ext = c->L >= 8 && c->L <= BFHE_MAX_L_UNROLLED && c->ext_QB.fast_ok && c->ext_BQ.fast_ok;
     c->d_tmod = base + o_tmod;
     c->d_delta_q = base + o_delta;
     c->d_Qinv_b = base + o_Qinvb;
@@ -643,6 +646,11 @@ extern "C" void bfhe_ctx_destroy(bfhe_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->tile_exec) cudaGraphExecDestroy(ctx->tile_exec);
+    if (ctx->cap_in) cudaEventDestroy(ctx->cap_in);
+    if (ctx->cap_out) cudaEventDestroy(ctx->cap_out);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    cudaFree(ctx->d_cbase);
     delete ctx;
 }
 

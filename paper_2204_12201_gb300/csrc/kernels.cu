@@ -229,6 +229,30 @@ __global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, in
     }
 }
 
+// the same inner product for 17 or more data primes (insecure test-only parameter sets): sizes at run time,
+// one thread per (ciphertext, word), the key re-read per ciphertext
+__global__ void k_inner_n(const u64* Dg, const u64* rlk, u64* W, int n, int QP, int L, PrimeTab tab, int N) {
+    const size_t plane = (size_t)QP * N;
+    const size_t total = plane * n;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t off = idx % plane;
+        const size_t c = idx / plane;
+        const int k = (int)(off / N);
+        const u64 q = tab.q[k], qinv = tab.qinv[k];
+        const u64* d = Dg + c * L * plane + off;
+        u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll 1
+        for (int j = 0; j < L; ++j) {
+            const u64 dj = d[(size_t)j * plane];
+            mac128(h0, l0, dj, rlk[((size_t)j * 2 + 0) * plane + off]);
+            mac128(h1, l1, dj, rlk[((size_t)j * 2 + 1) * plane + off]);
+        }
+        W[(c * 2 + 0) * plane + off] = redc(h0, l0, q, qinv);
+        W[(c * 2 + 1) * plane + off] = redc(h1, l1, q, qinv);
+    }
+}
+
 // ---------------------------------------------------------------- encode/decode, encrypt, keygen
 __global__ void k_permute(const u64* in, u64* out, const uint32_t* brv, int n, int scatter, int N, u64 t,
                           uint32_t* flags) {
@@ -439,7 +463,9 @@ __global__ void k_probe_modmul(u64* out, uint32_t iters, u64 q, u64 w, u64 ws) {
 }
 
 // trivial ciphertexts (Delta bit_k(c_base + c), 0), layout [s][C][n][2][L][N]
-__global__ void k_trivial_bits(u64* out, uint32_t s, u64 c_base, int C, size_t n, int L, const u64* delta, int N) {
+__global__ void k_trivial_bits(u64* out, uint32_t s, u64 c_base, const u64* cbp, int C, size_t n, int L,
+                               const u64* delta, int N) {
+    if (cbp) c_base = *cbp;
     const size_t ctw = (size_t)2 * L * N;
     const size_t total = (size_t)s * C * n * ctw;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -456,8 +482,9 @@ __global__ void k_trivial_bits(u64* out, uint32_t s, u64 c_base, int C, size_t n
 }
 
 // bits[k][i] += sum over c of src (PAPER: src [s][C][n]; SELECT: src [C][n], only if bit k of c)
-__global__ void k_accumulate(u64* bits, const u64* src, uint32_t s, u64 c_base, int C, size_t n, int select,
-                             int L, const u64* qtab, int N) {
+__global__ void k_accumulate(u64* bits, const u64* src, uint32_t s, u64 c_base, const u64* cbp, int C, size_t n,
+                             int select, int L, const u64* qtab, int N) {
+    if (cbp) c_base = *cbp;
     const size_t ctw = (size_t)2 * L * N;
     const size_t words = n * ctw;
     const size_t total = (size_t)s * words;
@@ -479,8 +506,9 @@ __global__ void k_accumulate(u64* bits, const u64* src, uint32_t s, u64 c_base, 
 }
 
 // out[c][i] = x[i] - (c_base + c)   (layout [C][n])
-__global__ void k_sub_const_chains(const u64* x, u64* out, u64 c_base, int C, size_t n, int L, const u64* qtab,
-                                   const u64* delta, u64 t, int N) {
+__global__ void k_sub_const_chains(const u64* x, u64* out, u64 c_base, const u64* cbp, int C, size_t n, int L,
+                                   const u64* qtab, const u64* delta, u64 t, int N) {
+    if (cbp) c_base = *cbp;
     const size_t ctw = (size_t)2 * L * N;
     const size_t words = n * ctw;
     const size_t total = (size_t)C * words;
@@ -499,6 +527,9 @@ __global__ void k_sub_const_chains(const u64* x, u64* out, u64 c_base, int C, si
         out[idx] = v;
     }
 }
+
+// one device word (the candidate base read by a replayed mod_to_bits tile)
+__global__ void k_set_word(u64* w, u64 v) { *w = v; }
 
 }  // namespace
 
@@ -573,12 +604,16 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
         case 14: return FN<14>(__VA_ARGS__);                                                                   \
         case 15: return FN<15>(__VA_ARGS__);                                                                   \
         case 16: return FN<16>(__VA_ARGS__);                                                                   \
-        default: return set_error(BFHE_EINVAL, "unsupported number of data primes");                         \
+        default: break;                                                                                        \
     }
 
 int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
     ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
     SWITCH_L(ctx->L, run_inner, ctx, Dg, W, n, st)
+    if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
+    const int QP = (int)(ctx->L + ctx->alpha);
+    LAUNCH(k_inner_n, (size_t)QP * ctx->N * n, Dg, ctx->d_rlk_ntt, W, n, QP, (int)ctx->L, ctx->tab, (int)ctx->N);
+    return BFHE_OK;
 }
 
 int launch_permute(const bfhe_ctx* ctx, const u64* in, u64* out, int n, int scatter, cudaStream_t st) {
@@ -645,23 +680,30 @@ int launch_gate_epilogue(const bfhe_ctx* ctx, u64* wires, size_t n, const int32_
     return BFHE_OK;
 }
 
-int launch_trivial_bits(const bfhe_ctx* ctx, u64* out, uint32_t s, u64 c_base, int C, size_t n, cudaStream_t st) {
-    LAUNCH(k_trivial_bits, (size_t)s * C * n * ctx->ct_words(), out, s, c_base, C, n, (int)ctx->L, ctx->d_delta_q,
+int launch_trivial_bits(const bfhe_ctx* ctx, u64* out, uint32_t s, u64 c_base, const u64* cbp, int C, size_t n,
+                        cudaStream_t st) {
+    LAUNCH(k_trivial_bits, (size_t)s * C * n * ctx->ct_words(), out, s, c_base, cbp, C, n, (int)ctx->L, ctx->d_delta_q,
            (int)ctx->N);
     return BFHE_OK;
 }
 
-int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s, u64 c_base, int C, size_t n,
-                      int select, cudaStream_t st) {
-    LAUNCH(k_accumulate, (size_t)s * n * ctx->ct_words(), bits, src, s, c_base, C, n, select, (int)ctx->L, ctx->tab.q,
+int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s, u64 c_base, const u64* cbp, int C,
+                      size_t n, int select, cudaStream_t st) {
+    LAUNCH(k_accumulate, (size_t)s * n * ctx->ct_words(), bits, src, s, c_base, cbp, C, n, select, (int)ctx->L, ctx->tab.q,
            (int)ctx->N);
     return BFHE_OK;
 }
 
-int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, int C, size_t n,
+int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, const u64* cbp, int C, size_t n,
                             cudaStream_t st) {
-    LAUNCH(k_sub_const_chains, (size_t)C * n * ctx->ct_words(), x, out, c_base, C, n, (int)ctx->L, ctx->tab.q,
+    LAUNCH(k_sub_const_chains, (size_t)C * n * ctx->ct_words(), x, out, c_base, cbp, C, n, (int)ctx->L, ctx->tab.q,
            ctx->d_delta_q, ctx->t, (int)ctx->N);
+    return BFHE_OK;
+}
+
+int launch_set_word(u64* w, u64 v, cudaStream_t st) {
+    k_set_word<<<1, 1, 0, st>>>(w, v);
+    BFHE_LAUNCH_CHECK("k_set_word");
     return BFHE_OK;
 }
 

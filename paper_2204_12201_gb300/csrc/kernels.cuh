@@ -50,10 +50,13 @@ int launch_gather(const bfhe_ctx* ctx, u64* dst, const u64* wires, size_t n, con
                   int field, int sub_field, cudaStream_t st);
 int launch_gate_epilogue(const bfhe_ctx* ctx, u64* wires, size_t n, const int32_t* table, int n_gates,
                          const u64* prod, int n_mul, cudaStream_t st);
-// mod_to_bits helpers
-int launch_trivial_bits(const bfhe_ctx* ctx, u64* out, uint32_t s, u64 c_base, int C, size_t n, cudaStream_t st);
-int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s, u64 c_base, int C, size_t n,
-                      int select, cudaStream_t st);
-int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, int C, size_t n,
+// mod_to_bits helpers; the candidate base is c_base, or the device word *cbp when cbp is not null
+// (a tile replayed from a CUDA graph reads its base from device memory)
+int launch_trivial_bits(const bfhe_ctx* ctx, u64* out, uint32_t s, u64 c_base, const u64* cbp, int C, size_t n,
+                        cudaStream_t st);
+int launch_accumulate(const bfhe_ctx* ctx, u64* bits, const u64* src, uint32_t s, u64 c_base, const u64* cbp, int C,
+                      size_t n, int select, cudaStream_t st);
+int launch_sub_const_chains(const bfhe_ctx* ctx, const u64* x, u64* out, u64 c_base, const u64* cbp, int C, size_t n,
                             cudaStream_t st);
+int launch_set_word(u64* w, u64 v, cudaStream_t st);
 int launch_probe_modmul(u64* out, int blocks, int threads, uint32_t iters, u64 q, u64 w, u64 ws, cudaStream_t st);

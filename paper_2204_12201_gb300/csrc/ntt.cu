@@ -4,7 +4,7 @@
 // reversed evaluation order out); butterfly on bit b of the index with
 // twiddle psi^brv((N + j) >> (b + 1)) and one Shoup product.  The forward
 // butterfly (X, Y) -> (X + T, X - T + 4q), T = Shoup(Y) in [0, 4q) (the
-// quotient estimate may be up to three short, see shoup_lazy4), grows the
+// quotient estimate may be up to three short, see shoup_lazy4n), grows the
 // bound by 4q per stage and is never reduced in between: from inputs < 4q,
 // 15 stages stay below 64q <= 2^64 for q < 2^58, and one Barrett-style
 // reduction at the end makes the output canonical.  Inverse: a_m = N^-1 psi^-m sum_k a^_k
@@ -88,7 +88,7 @@ __device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx) {
 template <int LOG_E, int W_LO, int HI, int LO>
 __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q4 = 4 * q;
+    const u64 q4 = 4 * q, nq = 0 - q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = HI - st;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
                 const u64 X = x[e];
-                const u64 T = shoup_lazy4(x[e2], wp.x, wp.y, q);
+                const u64 T = shoup_lazy4n(x[e2], wp.x, wp.y, nq);
                 x[e] = X + T;
                 x[e2] = X + q4 - T;
             }
@@ -130,7 +130,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const u64 X = in[base + (e << W_LO)];
-                const u64 T = shoup_lazy4(in[M + base + (e << W_LO)], w1.x, w1.y, q);
+                const u64 T = shoup_lazy4n(in[M + base + (e << W_LO)], w1.x, w1.y, 0 - q);
                 x[e] = half ? X + q4 - T : X + T;
             }
             // both halves of the limb are read before either CTA writes (in-place transforms)
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 && LOG_M - L
 template <int LOG_E, int W_LO, int LO, int HI>
 __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const ulonglong2* __restrict__ itw, u64 q) {
     constexpr int E = 1 << LOG_E;
-    const u64 q4 = 4 * q;
+    const u64 q4 = 4 * q, nq = 0 - q;
 #pragma unroll
     for (int st = 0; st <= HI - LO; ++st) {
         const int b = LO + st;
@@ -198,7 +198,7 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const
                 const int e = (g << (h + 1)) | r;
                 const int e2 = e | (1 << h);
                 const u64 U = x[e];
-                const u64 T = shoup_lazy4(x[e2], wp.x, wp.y, q);
+                const u64 T = shoup_lazy4n(x[e2], wp.x, wp.y, nq);
                 x[e] = U + T;
                 x[e2] = U + q4 - T;
             }
@@ -208,7 +208,9 @@ __device__ __forceinline__ void inv_stages(u64 (&x)[1 << LOG_E], int base, const
 
 // MODE 1: the block is the whole limb; MODE 2: half `half` of a limb of N = 2M words,
 // whose outermost stage pairs with the partner CTA of the cluster.
-template <int LOG_M, int LOG_E, int P, int MODE, bool LAZY>
+// OUT 0: twisted, canonical; 1: twisted, below 2q; 2: not twisted (the consumer multiplies by the twist,
+// folded into a product it makes anyway): from inputs below q, 15 stages leave words below 61q < 2^64.
+template <int LOG_M, int LOG_E, int P, int MODE, int OUT>
 __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, const ulonglong2* itw,
                                          const ulonglong2* twist, u64 q, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
@@ -238,7 +240,7 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         __syncthreads();
-        inv_pass<LOG_M, LOG_E, P + 1, MODE, LAZY>(x, sm, tid, itw, twist, q, in, out, half);
+        inv_pass<LOG_M, LOG_E, P + 1, MODE, OUT>(x, sm, tid, itw, twist, q, in, out, half);
     } else if constexpr (MODE == 2) {
         // outermost stage across the halves: publish, read the partner's words at the same
         // block positions through distributed shared memory, finish, twist
@@ -254,32 +256,40 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
             const u64 other = peer[pb + poff<W_LO>(e)];
             const u64 U = half ? other : x[e], V = half ? x[e] : other;
             const ulonglong2 wp = __ldg(itw + M + j);
-            const u64 T = shoup_lazy4(V, wp.x, wp.y, q);
+            const u64 T = shoup_lazy4n(V, wp.x, wp.y, 0 - q);
             const u64 y = half ? U + q4 - T : U + T;
-            const ulonglong2 tw = __ldg(twist + j + half * M);
-            out[j] = LAZY ? shoup_lazy(y, tw.x, tw.y, q) : shoup(y, tw.x, tw.y, q);
+            if constexpr (OUT == 2) {
+                out[j] = y;
+            } else {
+                const ulonglong2 tw = __ldg(twist + j + half * M);
+                out[j] = OUT == 1 ? shoup_lazy(y, tw.x, tw.y, q) : shoup(y, tw.x, tw.y, q);
+            }
         }
         cl.sync();   // the partner has finished reading this CTA's shared memory
     } else {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int j = base + (e << W_LO);
-            const ulonglong2 tw = __ldg(twist + j);
-            out[j] = LAZY ? shoup_lazy(x[e], tw.x, tw.y, q) : shoup(x[e], tw.x, tw.y, q);
+            if constexpr (OUT == 2) {
+                out[j] = x[e];
+            } else {
+                const ulonglong2 tw = __ldg(twist + j);
+                out[j] = OUT == 1 ? shoup_lazy(x[e], tw.x, tw.y, q) : shoup(x[e], tw.x, tw.y, q);
+            }
         }
     }
 }
 
-template <int LOG_M, int LOG_E, int MODE, bool LAZY>
+template <int LOG_M, int LOG_E, int MODE, int OUT>
 __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (MODE == 2 && LOG_M < 14 && LOG_M - LOG_E <= 8 ? 2 : 1)) k_ntt_inv(NttArgs a) {
     extern __shared__ u64 sm[];
     const LimbPtrs lp = limb_ptrs(a, blockIdx.x);
     const int half = blockIdx.y;
     const u64 q = a.tab.q[lp.p];
     const ulonglong2* itw = reinterpret_cast<const ulonglong2*>(a.tab.itw) + (size_t)lp.p * a.N;
-    const ulonglong2* twist = reinterpret_cast<const ulonglong2*>(a.tab.twist) + ((size_t)lp.p * 2 + (a.mont ? 1 : 0)) * a.N;
+    const ulonglong2* twist = reinterpret_cast<const ulonglong2*>(a.tab.twist) + ((size_t)lp.p * 3 + (a.mont ? 1 : 0)) * a.N;
     u64 x[1 << LOG_E];
-    inv_pass<LOG_M, LOG_E, 0, MODE, LAZY>(x, sm, threadIdx.x, itw, twist, q, lp.in + ((size_t)half << LOG_M),
+    inv_pass<LOG_M, LOG_E, 0, MODE, OUT>(x, sm, threadIdx.x, itw, twist, q, lp.in + ((size_t)half << LOG_M),
                                     lp.out + ((size_t)half << LOG_M), half);
 }
 
@@ -323,7 +333,7 @@ int run_fwd(const NttArgs& a, int blocks, cudaStream_t st) {
     return BFHE_OK;
 }
 
-template <int LOG_M, int LOG_E, int MODE, bool LAZY>
+template <int LOG_M, int LOG_E, int MODE, int OUT>
 int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     constexpr int T = 1 << (LOG_M - LOG_E);
     // the cluster exchange needs the shared buffer even for a single pass
@@ -331,7 +341,7 @@ int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
     static std::atomic<uint64_t> attr{0};   // devices whose function attribute is set
     const int dev = a.device;
     if (!(attr.load() >> dev & 1)) {
-        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BFHE_CUDA(cudaFuncSetAttribute(k_ntt_inv<LOG_M, LOG_E, MODE, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
         attr.fetch_or(1ull << dev);
     }
@@ -348,10 +358,10 @@ int run_inv(const NttArgs& a, int blocks, cudaStream_t st) {
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_inv<LOG_M, LOG_E, MODE, LAZY>, a));
+        BFHE_CUDA(cudaLaunchKernelEx(&cfg, k_ntt_inv<LOG_M, LOG_E, MODE, OUT>, a));
         BFHE_LAUNCH_CHECK("k_ntt_inv (cluster)");
     } else {
-        k_ntt_inv<LOG_M, LOG_E, MODE, LAZY><<<dim3(blocks, 1), T, smem, st>>>(a);
+        k_ntt_inv<LOG_M, LOG_E, MODE, OUT><<<dim3(blocks, 1), T, smem, st>>>(a);
         BFHE_LAUNCH_CHECK("k_ntt_inv");
     }
     return BFHE_OK;
@@ -439,15 +449,20 @@ int run_fwd_any(const NttArgs& a, int blocks, cudaStream_t st, bool top, bool la
 #define FWD_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
         return run_fwd_any<LM, LE>(a, blocks, st, top, lazy);
+template <int LM, int LE, int MODE>
+int run_inv_out(const NttArgs& a, int blocks, cudaStream_t st, int out) {
+    if (out == 2) return run_inv<LM, LE, MODE, 2>(a, blocks, st);
+    return out == 1 ? run_inv<LM, LE, MODE, 1>(a, blocks, st) : run_inv<LM, LE, MODE, 0>(a, blocks, st);
+}
+
 template <int LM, int LE>
-int run_inv_any(const NttArgs& a, int blocks, cudaStream_t st, bool split, bool lazy) {
-    if (split) return lazy ? run_inv<LM, LE, 2, true>(a, blocks, st) : run_inv<LM, LE, 2, false>(a, blocks, st);
-    return lazy ? run_inv<LM, LE, 1, true>(a, blocks, st) : run_inv<LM, LE, 1, false>(a, blocks, st);
+int run_inv_any(const NttArgs& a, int blocks, cudaStream_t st, bool split, int out) {
+    return split ? run_inv_out<LM, LE, 2>(a, blocks, st, out) : run_inv_out<LM, LE, 1>(a, blocks, st, out);
 }
 
 #define INV_CASE(LM, LE)                                                                                   \
     if (log_m == LM && log_e == LE)                                                                         \
-        return run_inv_any<LM, LE>(a, blocks, st, split, lazy);
+        return run_inv_any<LM, LE>(a, blocks, st, split, out);
 
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
                    int lazy_out) {
@@ -479,8 +494,9 @@ int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
     const int blocks = n_polys * n_limbs;
     const int subs = (int)(ctx->N >> log_m);
     if (subs != 1 && subs != 2) return set_error(BFHE_EINVAL, "unsupported ring degree");
+    if (lazy_out < 0 || lazy_out > 2) return set_error(BFHE_EINVAL, "bad inverse output form");
     const bool split = subs == 2;
-    const bool lazy = a.lazy != 0;
+    const int out = lazy_out;
     INV_CASE(10, 3) INV_CASE(10, 4) INV_CASE(10, 5)
     INV_CASE(11, 3) INV_CASE(11, 4) INV_CASE(11, 5)
     INV_CASE(12, 3) INV_CASE(12, 4) INV_CASE(12, 5)

@@ -34,3 +34,15 @@ def weights(seed, n_classes, n_tags, n_targets, n_ind):
     [n_classes][n_tags][n_ind * n_targets]."""
     w = rng(seed).integers(0, 64, size=(n_classes, n_tags, n_targets), dtype=np.int64)
     return np.repeat(w[:, :, None, :], n_ind, axis=2).reshape(n_classes, n_tags, n_ind * n_targets)
+
+
+def residues(seed, n, primes, N, comps=2):
+    """n ciphertext-shaped arrays [n][comps][len(primes)][N] of residues uniform in [0, q_i) per limb (random
+    ciphertexts: valid multiply inputs that decrypt to nothing in particular)."""
+    g = rng(seed)
+    out = np.empty((n, comps, len(primes), N), dtype=np.int64)
+    for c in range(n):
+        for k in range(comps):
+            for i, q in enumerate(primes):
+                out[c, k, i] = g.integers(0, q, size=N, dtype=np.int64)
+    return out

@@ -45,7 +45,7 @@ def _lib():
 def test_context_parameters_are_validated_on_the_host():
     """Every rejected parameter set returns BFHE_EINVAL before any CUDA call (runs without a GPU)."""
     lib, bfhe = _lib()
-    bad = [dict(N=1000), dict(N=512), dict(N=65536), dict(L=0), dict(L=17), dict(alpha=0), dict(alpha=3),
+    bad = [dict(N=1000), dict(N=512), dict(N=65536), dict(L=0), dict(L=33), dict(alpha=0), dict(alpha=3),
            dict(prime_bits=29), dict(prime_bits=59), dict(t=65536), dict(t=17), dict(t=3), dict(t=1),
            dict(t=(1 << 32) + 15)]
     for over in bad:
@@ -85,7 +85,9 @@ def test_library_parameter_rule_matches_the_oracle():
     _, bfhe = _lib()
     cases = [(1024, 2, 1, 12289, 50), (1024, 3, 1, 65537, 50), (1024, 4, 2, 65537, 50), (1024, 16, 2, 65537, 50),
              (1024, 2, 1, 65537, 55), (1024, 3, 1, 2, 50), (4096, 2, 1, 65537, 50), (8192, 4, 1, 65537, 50),
-             (16384, 8, 1, 65537, 50), (32768, 16, 2, 65537, 50), (32768, 16, 1, 2, 50), (32768, 4, 2, 65537, 50)]
+             (16384, 8, 1, 65537, 50), (32768, 16, 2, 65537, 50), (32768, 16, 1, 2, 50), (32768, 4, 2, 65537, 50),
+             (1024, 3, 1, 4294957057, 50), (1024, 20, 2, 65537, 50), (1024, 32, 1, 65537, 50),
+             (16384, 20, 1, 65537, 50), (32768, 28, 1, 65537, 50)]
     for N, L, alpha, t, bits in cases:
         primes, K = bfhe.param_primes(N, L, alpha, t, bits)
         prm = Params(N=N, L=L, alpha=alpha, t=t, prime_bits=bits)
