@@ -109,6 +109,17 @@ int bfhe_check(bfhe_ctx* ctx, void* stream, uint32_t* flags_out);
  * growth, hence device synchronisation, inside later calls). */
 int bfhe_reserve(bfhe_ctx* ctx, size_t n);
 
+/* Device memory the context holds, in bytes (host buffer of 4): out[0] the
+ * constant tables (moduli, twiddles, twists, extension tables), out[1] the
+ * keys (0 before keygen), out[2] the scratch arena (it grows to the largest
+ * call and does not shrink), out[3] other small buffers.  For admission
+ * control by device memory (serving); the paper has no counterpart. */
+int bfhe_ctx_device_bytes(const bfhe_ctx* ctx, size_t* out);
+
+/* Scratch bytes one mul_relin of n ciphertexts uses (its arena share; calls
+ * beyond the scratch budget run in tiles of this size); 0 for a NULL context. */
+size_t bfhe_mul_scratch_bytes(const bfhe_ctx* ctx, size_t n);
+
 /* Guarded fast base extension inside the multiply.  The
  * exact extensions of the lift (Q -> B) and of the scale-and-round (Q -> B,
  * B -> Q) normally run Garner's mixed-radix digits.  With this on they first
@@ -154,6 +165,14 @@ int bfhe_graph_tiles(const bfhe_ctx* ctx);
  * using the library. */
 int bfhe_set_scratch_budget(size_t bytes);
 size_t bfhe_scratch_budget(void);
+
+/* Most ciphertexts one multiply launch sequence takes at ring degree 2^logN
+ * (process-wide; 0, the default, means as many as the scratch budget holds).
+ * Larger batches run in tiles of this size; results do not depend on it.
+ * The autotuner sets it (paper_2204_12201_gb300/autotune.py).  BFHE_EINVAL
+ * for logN outside [10, 15]; bfhe_mul_tile returns the setting. */
+int bfhe_set_mul_tile(uint32_t logN, size_t max_ct);
+size_t bfhe_mul_tile(uint32_t logN);
 
 /* Key generation from `seed` (keys stay resident on the device): secret s
  * ternary, pk = ([-(a s + e)]_Q, a), relinearisation keys for the RNS digits

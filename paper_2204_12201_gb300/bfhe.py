@@ -43,6 +43,8 @@ def load():
         "bfhe_ctx_destroy": (None, [P]),
         "bfhe_ctx_primes": (I, [P, P, P]),
         "bfhe_reserve": (I, [P, S]),
+        "bfhe_ctx_device_bytes": (I, [P, P]),
+        "bfhe_mul_scratch_bytes": (S, [P, S]),
         "bfhe_keygen": (I, [P, U64, P]),
         "bfhe_export_keys": (I, [P, P, P, P, P]),
         "bfhe_encrypt": (I, [P, P, S, U64, P, P]),
@@ -78,6 +80,8 @@ def load():
         "bfhe_set_graph_tiles": (I, [P, I]),
         "bfhe_graph_tiles": (I, [P]),
         "bfhe_scratch_budget": (S, []),
+        "bfhe_set_mul_tile": (I, [U32, S]),
+        "bfhe_mul_tile": (S, [U32]),
         "bfhe_ntt_config": (I, [U32, I, U32, U32, P, P]),
         "bfhe_strerror": (ctypes.c_char_p, [I]),
         "bfhe_last_error": (ctypes.c_char_p, []),
@@ -185,6 +189,16 @@ class Context:
 
     def reserve(self, n):
         _check(self.lib.bfhe_reserve(self.h, n))
+
+    def device_bytes(self):
+        """{tables, keys, scratch, other}: device memory the context holds (bytes)."""
+        out = (ctypes.c_size_t * 4)()
+        _check(self.lib.bfhe_ctx_device_bytes(self.h, out))
+        return {"tables": out[0], "keys": out[1], "scratch": out[2], "other": out[3]}
+
+    def mul_scratch_bytes(self, n):
+        """Scratch one mul_relin of n ciphertexts uses."""
+        return int(self.lib.bfhe_mul_scratch_bytes(self.h, n))
 
     def keygen(self, seed):
         _check(self.lib.bfhe_keygen(self.h, seed, self.stream))
@@ -383,6 +397,15 @@ def ntt_config(logN, inverse, log_m=0, log_e=0):
     m, e = ctypes.c_uint32(), ctypes.c_uint32()
     _check(load().bfhe_ntt_config(logN, int(inverse), log_m, log_e, ctypes.byref(m), ctypes.byref(e)))
     return m.value, e.value
+
+
+def set_mul_tile(logN, max_ct):
+    """Most ciphertexts per multiply launch sequence at ring degree 2^logN (0: as the scratch allows)."""
+    _check(load().bfhe_set_mul_tile(logN, max_ct))
+
+
+def mul_tile(logN):
+    return int(load().bfhe_mul_tile(logN))
 
 
 def set_scratch_budget(nbytes):

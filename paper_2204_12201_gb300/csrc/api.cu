@@ -31,6 +31,10 @@ size_t g_scratch_budget = (size_t)16 << 30;
 
 size_t mul_words_per_ct(const bfhe_ctx* c) { return mul_scratch_bytes(c, 1) / sizeof(u64); }
 
+// most ciphertexts per multiply launch sequence, per log2 N (0: as many as the scratch holds); set by the
+// autotuner through bfhe_set_mul_tile
+size_t g_mul_tile[16] = {};
+
 // out[i] = a[i] * b[i] (relinearised), n ciphertexts, scratch of `scratch_words` words
 int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, u64* scratch,
                    size_t scratch_words, cudaStream_t st) {
@@ -38,6 +42,7 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
     const size_t per = mul_words_per_ct(c);
     size_t tile = scratch_words / per;
     if (tile == 0) return set_error(BFHE_ENOMEM, "scratch too small for one multiply");
+    if (c->logN < 16 && g_mul_tile[c->logN] && g_mul_tile[c->logN] < tile) tile = g_mul_tile[c->logN];
     const size_t ctw = c->ct_words();
     for (size_t c0 = 0; c0 < n; c0 += tile) {
         const int m = (int)std::min(tile, n - c0);
@@ -208,6 +213,14 @@ extern "C" int bfhe_set_scratch_budget(size_t bytes) {
 }
 
 extern "C" size_t bfhe_scratch_budget(void) { return g_scratch_budget; }
+
+extern "C" int bfhe_set_mul_tile(uint32_t logN, size_t max_ct) {
+    if (logN < 10 || logN > 15) return set_error(BFHE_EINVAL, "logN must be in [10, 15]");
+    g_mul_tile[logN] = max_ct;
+    return BFHE_OK;
+}
+
+extern "C" size_t bfhe_mul_tile(uint32_t logN) { return logN < 16 ? g_mul_tile[logN] : 0; }
 
 extern "C" int bfhe_reserve(bfhe_ctx* c, size_t n) {
     CHECK_CTX(c);

@@ -157,6 +157,7 @@ struct bfhe_ctx {
     std::vector<uint32_t> brv;   // host copy of bit reversal (N)
 
     void* d_arena = nullptr;     // all constant tables
+    size_t arena_bytes = 0;
     PrimeTab tab{};
     uint32_t* d_brv = nullptr;   // [N]
     ExtDesc ext_QB{}, ext_BQ{}, ext_PQ{}, ext_Qt{};

@@ -605,6 +605,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
         delete c;
         return rc;
     }
+    c->arena_bytes = ar.words.size() * sizeof(u64);
     const u64* base = (const u64*)c->d_arena;
     c->tab.q = base + o_q;
     c->tab.qinv = base + o_qinv;
@@ -653,6 +654,18 @@ extern "C" void bfhe_ctx_destroy(bfhe_ctx* ctx) {
     cudaFree(ctx->d_cbase);
     delete ctx;
 }
+
+extern "C" int bfhe_ctx_device_bytes(const bfhe_ctx* ctx, size_t* out) {
+    if (!ctx || !out) return set_error(BFHE_EINVAL, "null argument");
+    const size_t N = ctx->N, L = ctx->L, QP = ctx->L + ctx->alpha;
+    out[0] = ctx->arena_bytes + 256;   // tables and the flag word
+    out[1] = ctx->d_sk ? (N + QP * N + 4 * L * N + 2 * L * QP * N) * sizeof(u64) : 0;
+    out[2] = ctx->scratch_bytes;
+    out[3] = ctx->d_cbase ? sizeof(u64) : 0;
+    return BFHE_OK;
+}
+
+extern "C" size_t bfhe_mul_scratch_bytes(const bfhe_ctx* ctx, size_t n) { return ctx ? mul_scratch_bytes(ctx, n) : 0; }
 
 extern "C" int bfhe_ctx_primes(const bfhe_ctx* ctx, uint64_t* primes_out, uint32_t* K_out) {
     if (!ctx || !primes_out) return set_error(BFHE_EINVAL, "null argument");

@@ -20,26 +20,51 @@ class FakeEvent:
 
 
 class FakeBackend:
-    """Ciphertexts are int64 arrays [n][4]; squaring is elementwise mod P."""
+    """Ciphertexts are int64 arrays [n][4]; squaring is elementwise mod P.  The multiply's arena grows to the
+    largest batch (N bytes per ciphertext) and never shrinks, like the library's."""
 
-    def __init__(self):
+    FERMAT = 3
+
+    def __init__(self, resident=1000):
         self.calls = []
+        self.arena = {}
+        self.resident = resident
 
     def ct_bytes(self, N):
         return N
 
-    def mul_scalar_bytes(self, N, n):
-        return 0
-
     def mul_scratch_bytes(self, N, n):
         return n * N
 
-    def encrypt(self, req):
+    def resident_bytes(self):
+        return self.resident
+
+    def arena_bytes(self, N):
+        return self.arena.get(N, 0)
+
+    def cache_bytes(self):
+        return 0
+
+    def fermat_depth(self, N):
+        return self.FERMAT
+
+    def slots(self, req):
         g = np.random.Generator(np.random.PCG64(req.seed))
-        return g.integers(0, P, size=(req.n, 4), dtype=np.int64)
+        return g.integers(0, P if req.kind == "chain" else 1 << req.s, size=(req.n, 4), dtype=np.int64)
+
+    def encrypt(self, req):
+        return self.slots(req)
+
+    def chains(self, N, x, C):
+        return np.concatenate([(x - c) % P for c in range(C)])
+
+    def finish(self, N, d, n, s):
+        eq = (1 - d) % P
+        return np.stack([sum(eq[c * n:(c + 1) * n] for c in range(1 << s) if (c >> k) & 1) % P for k in range(s)])
 
     def square(self, N, x):
         self.calls.append((N, x.shape[0]))
+        self.arena[N] = max(self.arena.get(N, 0), self.mul_scratch_bytes(N, x.shape[0]))
         return (x * x) % P
 
     def cat(self, N, xs):
@@ -65,7 +90,13 @@ class FakeClock:
 
 
 def expected(req):
-    x = FakeBackend().encrypt(req)
+    b = FakeBackend()
+    x = b.encrypt(req)
+    if req.kind == "bridge":
+        d = b.chains(req.N, x, 1 << req.s)
+        for _ in range(b.FERMAT):
+            d = (d * d) % P
+        return b.finish(req.N, d, req.n, req.s)
     for _ in range(req.depth):
         x = (x * x) % P
     return x
@@ -88,31 +119,71 @@ def test_continuous_batching_matches_alone_and_batches_across_requests():
 
 
 def test_admission_respects_the_memory_budget():
+    """What the device holds (resident tables, the arenas as grown by the batches, the active buffers) stays
+    within the budget at every step."""
     reqs = serving.poisson_stream(4, 20, rate=5000.0, ring_degrees=(4096,), depth=(2, 4), cts=(2, 3))
     b = FakeBackend()
     clk = FakeClock()
     srv = serving.Server(b, mem_budget_bytes=0)
-    one = max(srv.need(r) for r in reqs)
+    one = max(srv.need(r) + b.mul_scratch_bytes(r.N, r.units()) for r in reqs) + b.resident
     srv.budget = 2 * one
-    peak = []
+    held = []
     orig = b.square
 
     def square(N, x):
-        peak.append(srv.used)
-        return orig(N, x)
+        y = orig(N, x)
+        held.append(b.resident + srv.used + sum(b.arena.values()))
+        return y
 
     b.square = square
     done = srv.run(copy.deepcopy(reqs), clock=clk, sleep=clk.sleep)
     assert len(done) == len(reqs)
-    assert max(peak) <= srv.budget
+    assert max(held) <= srv.budget and srv.peak <= srv.budget
     assert srv.used == 0
     for r in done:
         assert np.array_equal(r.result, expected(r))
 
 
+def test_arena_growth_is_charged_on_admission():
+    """Two requests whose buffers fit together, but whose joint batch would grow the arena past the budget,
+    run one after the other; once the arena has grown it stays charged."""
+    r1 = serving.Request(rid=0, N=4096, depth=3, n=4, arrival=0.0, seed=1)
+    r2 = serving.Request(rid=1, N=4096, depth=3, n=4, arrival=0.0001, seed=2)
+    b = FakeBackend(resident=0)
+    srv = serving.Server(b, mem_budget_bytes=0)
+    alone = srv.need(r1) + b.mul_scratch_bytes(4096, 4)
+    srv.budget = alone + srv.need(r2) + b.mul_scratch_bytes(4096, 2)   # room for both buffers, not both batches
+    clk = FakeClock()
+    done = srv.run([r1, r2], clock=clk, sleep=clk.sleep)
+    assert max(n for _, n in b.calls) == 4          # never one batch of 8
+    by = {r.rid: r for r in done}
+    assert by[1].t_admit >= by[0].t_done
+    for r in done:
+        assert np.array_equal(r.result, expected(r))
+
+
+def test_bridge_requests_batch_with_chains():
+    """Bridge conversions (select mode from differences, squarings and sums) share the batched squarings
+    with the chain requests of their ring and give the same bits as alone."""
+    reqs = serving.poisson_stream(9, 24, rate=3000.0, ring_degrees=(4096, 8192), depth=(1, 4), cts=(1, 8),
+                                  bridge=0.5, bits=(1, 3))
+    assert any(r.kind == "bridge" for r in reqs) and any(r.kind == "chain" for r in reqs)
+    b = FakeBackend()
+    clk = FakeClock()
+    srv = serving.Server(b, mem_budget_bytes=10**9)
+    done = srv.run(copy.deepcopy(reqs), clock=clk, sleep=clk.sleep)
+    assert len(done) == len(reqs)
+    for r in done:
+        assert np.array_equal(r.result, expected(r)), r.rid
+    assert srv.muls == sum(r.units() * r.depth for r in done)
+    seq = serving.serve_sequential(FakeBackend(), copy.deepcopy(reqs), clock=clk, sleep=clk.sleep)
+    for r in seq:
+        assert np.array_equal(r.result, expected(r))
+
+
 def test_request_larger_than_budget_is_rejected():
     reqs = serving.poisson_stream(5, 2, rate=10.0, ring_degrees=(4096,), depth=(1, 1), cts=(8, 8))
-    srv = serving.Server(FakeBackend(), mem_budget_bytes=10)
+    srv = serving.Server(FakeBackend(), mem_budget_bytes=2000)
     with pytest.raises(ValueError):
         srv.run(reqs)
 
@@ -134,7 +205,7 @@ def test_admission_is_first_come_first_served():
     b = FakeBackend()
     clk = FakeClock()
     srv = serving.Server(b, mem_budget_bytes=0)
-    srv.budget = 2 * max(srv.need(r) for r in reqs)
+    srv.budget = b.resident + 2 * max(srv.need(r) + b.mul_scratch_bytes(r.N, r.units()) for r in reqs)
     done = srv.run(copy.deepcopy(reqs), clock=clk, sleep=clk.sleep)
     admitted = sorted(done, key=lambda r: (r.t_admit, r.arrival))
     assert [r.rid for r in admitted] == [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]
@@ -158,16 +229,25 @@ def test_gpu_result_is_the_same_alone_and_in_the_mix():
         pytest.skip("no CUDA device")
     import __graft_entry__
     __graft_entry__.build()
+    from paper_2204_12201_gb300 import bfhe
     b = serving.GpuBackend(ring_degrees=(4096, 8192))
-    reqs = serving.poisson_stream(7, 10, rate=500.0, ring_degrees=(4096, 8192), depth=(1, 2), cts=(1, 4))
+    reqs = serving.poisson_stream(7, 12, rate=500.0, ring_degrees=(4096, 8192), depth=(1, 2), cts=(1, 4),
+                                  bridge=0.3, bits=(1, 2))
+    assert any(r.kind == "bridge" for r in reqs)
     mixed = serving.Server(b, 8 << 30).run(copy.deepcopy(reqs))
     alone = serving.serve_sequential(b, copy.deepcopy(reqs))
     by_id = {r.rid: r for r in alone}
     for r in mixed:
         assert torch.equal(r.result, by_id[r.rid].result)
-        # and it decrypts to the slot values raised to 2^depth
         slots = b.slots(r)
-        got = b.ctx[r.N].decrypt(r.result.contiguous()).cpu().numpy()
+        ctx = b.ctx[r.N]
+        if r.kind == "bridge":
+            # the library's own conversion (Listing 8, select mode) of the same encrypted input, word for word
+            want = ctx.mod_to_bits(b.encrypt(r), r.s, 0, (1 << r.s) - 1, bfhe.SELECT)
+            assert torch.equal(r.result, want)
+            continue
+        # a chain decrypts to the slot values raised to 2^depth
+        got = ctx.decrypt(r.result.contiguous()).cpu().numpy()
         want = slots.copy()
         for _ in range(r.depth):
             want = (want * want) % 65537
