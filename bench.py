@@ -498,7 +498,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    shapes = autotune.tune(ring_degrees=(8192, 16384))     # NTT block shapes for the rings used here
+    tuned = autotune.tune(ring_degrees=(4096, 8192, 16384, 32768))   # NTT shapes and multiply tiles
     ctx = bfhe.Context(N=WL["N"], L=WL["L"], alpha=WL["alpha"], t=WL["t"], device=local)
     ctx.keygen(1 + rank)
     job = workloads.GenotypeJob(ctx, n_tags=N_TAGS, s_bits=S_BITS)
@@ -594,7 +594,8 @@ def main():
                 "config": {**base_config(), "mul_relin_per_step": n_mul // args.steps, "mul_relin_mix": mix,
                            "base_extension": "guarded fast, exact fallback" if ctx.fast_extension else "exact Garner",
                            "parallelism": "replicas" if world > 1 else "single",
-                           "ntt_shapes": {k: v["shape"] for k, v in shapes.items()},
+                           "autotuned": {str(k): {"ntt_fwd": v["fwd"], "ntt_inv": v["inv"], "mul_tile": v["tile"]}
+                                         for k, v in tuned.items()},
                            "l2": "no flush: per-step working set > 10 GB >> 129 MB L2"},
                 "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu_line, "ops_per_step": {"add": n_add // args.steps, "sub": n_sub // args.steps,

@@ -312,10 +312,10 @@ int bfhe_mod_to_sint(bfhe_ctx* ctx, const uint64_t* x, uint32_t s, uint64_t pos_
 
 /* Allocation-free variant of bfhe_mul_relin.  The paper has no counterpart:
  * this is for callers that cannot allocate device memory at call time --
- * code running under CUDA stream capture (where cudaMalloc and the device
- * synchronisation that growing the context scratch needs are not allowed),
- * and deployments that reserve all device memory at start-up and forbid
- * allocation afterwards.  Same arguments and result as bfhe_mul_relin (bit
+ * deployments that reserve all device memory at start-up and forbid
+ * allocation afterwards, and host code whose hot path must not enter an
+ * allocator or wait for the device-wide synchronisation that growing the
+ * context's scratch arena takes.  Same arguments and result as bfhe_mul_relin (bit
  * identical), but the multiply's scratch is a fixed static device array of
  * BFHE_NOALLOC_SCRATCH_BYTES (32 MiB) instead of the context's arena; the
  * call makes no cudaMalloc, cudaFree or other allocating call.

@@ -1,10 +1,10 @@
 """bfhe_mul_relin_noalloc: the multiply for callers that cannot allocate.
 
 Some callers of this library may not allocate device memory when they call
-it: code recording a CUDA graph under stream capture (cudaMalloc and the
-device-wide synchronisation that growing the context's scratch arena needs
-are illegal there), and services that reserve all device memory at start-up
-and forbid allocation afterwards.  For them the library has one entry point
+it: services that reserve all device memory at start-up and forbid
+allocation afterwards, and host code whose hot path must not enter an
+allocator or wait for the device-wide synchronisation that growing the
+context's scratch arena takes.  For them the library has one entry point
 whose scratch is a fixed static device array instead of the arena.  These
 tests call it through the C ABI and check it against the ordinary
 bfhe_mul_relin, bit for bit (the tolerance of every parity test here: exact
