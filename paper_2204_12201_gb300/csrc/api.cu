@@ -74,7 +74,9 @@ int mul_relin_impl(bfhe_ctx* c, const u64* A, const u64* B, u64* out, size_t n, 
         io3.in_is = io3.out_is = LK * N;
         io3.in_ls = io3.out_ls = N;
         RC(launch_ntt_inv(c, io3, 3 * m, (int)LK, c->mapQB(), 1, st, 2));   // scale applies the twist
-        RC(launch_scale(c, X, C3, m, st));
+        // scale's intermediate y [m][3][K][N] (two-pass form) lives in the digit buffer, dead until the digit
+        // transforms
+        RC(launch_scale(c, X, C3, m, st, (L * QP >= 3 * K) ? Dg : nullptr));
         NttIO iod;   // digit j of c2 (limb j of C3 slot 2), reduced into every prime of Q u P
         iod.in = C3 + 2 * L * N;
         iod.out = Dg;

@@ -176,12 +176,14 @@ __global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, in
 
 // key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC).
 // A thread owns one word (k, coefficient) of Q u P: it keeps the 2L key words of that word in
-// registers and walks a group of ciphertexts, so the key is read once per group.  The digits of the
-// next D ciphertexts are in flight while the current one is accumulated (D = 2 while the registers
-// allow two CTAs of 256 threads per SM, else 1).
+// registers and walks a group of ciphertexts, so the key is read once per group.  Up to 8 data primes
+// the digits of the next two ciphertexts are in flight while the current one is accumulated; above 8
+// there is no look-ahead, so that two CTAs of 256 threads still fit an SM (at 16 primes: 166 -> 128
+// registers, +3% mul_relin at N = 32768).
 template <int L>
-__global__ void k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP, int cpg, PrimeTab tab, int N) {
-    constexpr int D = L <= 8 ? 2 : 1;
+__global__ void __launch_bounds__(256, 2) k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP,
+                                                              int cpg, PrimeTab tab, int N) {
+    constexpr int D = L <= 8 ? 2 : 0;
     const size_t plane = (size_t)QP * N;
     const int groups = (n + cpg - 1) / cpg;
     const size_t total = plane * groups;

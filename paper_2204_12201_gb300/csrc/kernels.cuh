@@ -22,7 +22,8 @@ int launch_pointwise(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* out, 
 // slots = 4 (a0 a1 b0 b1) or 2 (squaring: a0 a1 only)
 int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st);
 int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, int square, cudaStream_t st);
-int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st);
+// tmp: [n][3][K][N] words for the two-pass form (10 or more data primes), or null for one pass
+int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st, u64* tmp = nullptr);
 int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st);
 int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st);
 
