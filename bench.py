@@ -356,6 +356,11 @@ def extras(torch, bfhe, circuits, ctx16):
         out["bit_gates_per_s_%s_graph" % name] = net.n_mul / ms_gr * 1e3
         out["%s_gates" % name] = net.n_mul
         del comp
+        # the per-op baseline: one gate per call (one multiply launch sequence per gate)
+        po = circuits.Compiled(ctx8, net, 1, per_op=True)
+        po.set_inputs(ctx8.encrypt(ops, 9).view(net.n_inputs, 1, 2, 4, 8192))
+        out["bit_gates_per_s_%s_per_op" % name] = net.n_mul / timed(po.run, 1) * 1e3
+        del po
     ctx8.close()
     out["modmul_probe_per_s"] = bfhe.probe_modmul(torch.cuda.current_device())
     # Fibonacci (Listings 3 and 4), 8-bit words, 10 iterations, one input per slot, at the paper's

@@ -234,19 +234,29 @@ class Netlist:
 
 
 class Compiled:
-    """A netlist's level tables on the device, runnable eagerly or as a CUDA graph."""
+    """A netlist's level tables on the device, runnable eagerly or as a CUDA graph.
 
-    def __init__(self, ctx, net, n):
+    per_op=True runs one gate per call instead (the same schedule order, one bfhe_gate_level call and so one
+    multiply launch sequence per gate): the per-operation baseline the levelised batching is compared with."""
+
+    def __init__(self, ctx, net, n, per_op=False):
         if net.t != ctx.t:
             raise ValueError("netlist built for t = %d, context has t = %d" % (net.t, ctx.t))
         self.ctx, self.net, self.n = ctx, net, n
         self.calls = []      # (table tensor, n_gates, n_mul)
         for _, muls, subs in net.schedule():
+            if per_op:
+                for row in muls:
+                    self.calls.append(self._table([row], 1))
+                for s in subs:
+                    for row in s:
+                        self.calls.append(self._table([row], 0))
+                continue
             if muls:
                 self.calls.append(self._table(muls, len(muls)))
             for s in subs:
                 self.calls.append(self._table(s, 0))
-        self.depth = sum(1 for c in self.calls if c[2] > 0)
+        self.depth = sum(1 for _, muls, _ in net.schedule() if muls)
         self.wires = torch.zeros(net.n_wires, n, 2, ctx.L, ctx.N, dtype=torch.int64, device=ctx.device)
         self.graph = None
 

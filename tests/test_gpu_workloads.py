@@ -124,6 +124,10 @@ def test_circuits_match_the_oracle_eager_and_graph(small):
         comp.replay()
         torch.cuda.synchronize()
         assert torch.equal(comp.out(out), got)
+        per_op = circuits.Compiled(ctx, net, 1, per_op=True)     # one gate per call, same results
+        per_op.set_inputs(cts_to_device(prm, cts)[:, None])
+        per_op.run()
+        assert torch.equal(per_op.out(out), got) and per_op.depth == comp.depth
 
 
 def test_genotype_job_matches_the_oracle_pipeline(small):
