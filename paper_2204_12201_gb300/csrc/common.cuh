@@ -130,6 +130,14 @@ struct ExtDesc {
     int fast_ok;         // all moduli < 2^50: the fast path's tables are valid
 };
 
+// Host copies of the guarded fast extension's per-source tables and 26-bit limb pairs: the kernels take them
+// as a kernel parameter (constant bank), so that the inner products read their factors without a load
+struct ExtHost {
+    int n = 0, m = 0;
+    std::vector<uint32_t> c26;                       // [m][n][2]
+    std::vector<u64> qhinv, qhinv_s, g_hi, g_lo;     // [n]
+};
+
 // Device-side prime tables of a context, by prime index
 // (0..L-1 data, L..L+alpha-1 special, L+alpha..L+alpha+K-1 auxiliary, last: t).
 struct PrimeTab {
@@ -161,6 +169,7 @@ struct bfhe_ctx {
     PrimeTab tab{};
     uint32_t* d_brv = nullptr;   // [N]
     ExtDesc ext_QB{}, ext_BQ{}, ext_PQ{}, ext_Qt{};
+    ExtHost exth_QB, exth_BQ;
     // Shoup pair tables: p[i] = w_i, p[n + i] = ws_i
     const u64* d_tmod = nullptr;    // [nP] [t]_{prime}
     const u64* d_delta_q = nullptr; // [L]  [Delta]_{q_i}

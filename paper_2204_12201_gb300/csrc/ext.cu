@@ -75,21 +75,46 @@ __device__ __forceinline__ u64 ext_eval(const u64 (&v)[NS], bool neg, const ExtD
     return acc;
 }
 
+// The guarded fast extension's per-source factors and 26-bit limb pairs for NS sources and ND targets, passed by
+// value as a kernel parameter (it sits in the constant bank): with the loops over sources and targets unrolled,
+// every factor is an operand of the multiply-add that uses it, with no load instruction.
+template <int NS, int ND>
+struct FastTab {
+    uint2 c[ND][NS];        // (low, high) 26-bit limbs of [(S/s_i) 2^64]_{T_j}
+    u64 qh[NS], qhs[NS];    // [(S/s_i)^-1]_{s_i} and its Shoup companion
+    u64 ghi[NS], glo[NS];   // floor(2^128 / s_i): high and low words
+};
+
+template <int NS, int ND>
+FastTab<NS, ND> fast_tab(const ExtHost& h) {
+    FastTab<NS, ND> t{};
+    if (h.n != NS || h.m != ND) return t;   // only the instances the launchers use are ever filled
+    for (int j = 0; j < ND; ++j)
+        for (int i = 0; i < NS; ++i) t.c[j][i] = make_uint2(h.c26[((size_t)j * NS + i) * 2], h.c26[((size_t)j * NS + i) * 2 + 1]);
+    for (int i = 0; i < NS; ++i) {
+        t.qh[i] = h.qhinv[i];
+        t.qhs[i] = h.qhinv_s[i];
+        t.ghi[i] = h.g_hi[i];
+        t.glo[i] = h.g_lo[i];
+    }
+    return t;
+}
+
 // Guarded fast exact extension (all moduli below 2^50), first half: y_i = [x_i (S/s_i)^-1]_{s_i} split
 // into 26-bit limbs, and v = round(sum_i y_i / s_i) from the 64.64 fixed-point sum of
 // floor(y_i floor(2^128/s_i) / 2^64) (each term at most 2 units below y_i 2^64 / s_i).  Returns false
 // when the fraction lies within 2n + 2 units of 1/2: then the caller takes the exact mixed-radix path.
-template <int NS>
-__device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, uint32_t (&y0)[NS],
-                                          uint32_t (&y1)[NS], int& v) {
+template <int NS, int ND>
+__device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, const FastTab<NS, ND>& ft,
+                                          uint32_t (&y0)[NS], uint32_t (&y1)[NS], int& v) {
     u64 lo = 0, hi = 0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
         const u64 s = d.src_q[i];
-        const u64 y = shoup(x[i], d.qhinv[i], d.qhinv_s[i], s);
+        const u64 y = shoup(x[i], ft.qh[i], ft.qhs[i], s);
         y0[i] = (uint32_t)(y & 0x3FFFFFFull);
         y1[i] = (uint32_t)(y >> 26);
-        const u64 term = y * d.g_hi[i] + __umul64hi(y, d.g_lo[i]);
+        const u64 term = y * ft.ghi[i] + __umul64hi(y, ft.glo[i]);
         lo += term;
         hi += lo < term ? 1ull : 0ull;
     }
@@ -107,15 +132,13 @@ __device__ __forceinline__ bool fast_prep(const u64 (&x)[NS], const ExtDesc& d, 
 
 // second half: sum_i y_i [(S/s_i) 2^64]_{T_j} with the 26-bit limb products accumulated in four 64-bit
 // words (no carries below 2^13 sources), one Montgomery reduction, minus [v S]_{T_j}; canonical result
-template <int NS>
+template <int NS, int ND>
 __device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_t (&y1)[NS], int v, const ExtDesc& d,
-                                         int j) {
-    const uint2* c = reinterpret_cast<const uint2*>(d.c26) + (size_t)j * NS;   // (low, high) limb pairs, 8-byte aligned
+                                         const FastTab<NS, ND>& ft, int j) {
     u64 p00 = 0, p01 = 0, p10 = 0, p11 = 0;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        const uint2 cc = __ldg(c + i);
-        const uint32_t c0 = cc.x, c1 = cc.y;
+        const uint32_t c0 = ft.c[j][i].x, c1 = ft.c[j][i].y;
         p00 += (u64)y0[i] * c0;
         p01 += (u64)y0[i] * c1;
         p10 += (u64)y1[i] * c0;
@@ -133,8 +156,8 @@ __device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_
 
 // X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
 template <int NS, bool FAST>
-__global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
-                        uint32_t* flags) {
+__global__ void __launch_bounds__(256, NS <= 8 ? 4 : 2) k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
+                        uint32_t* flags, FastTab<FAST ? NS : 1, FAST ? NS + 1 : 1> ft) {
     const size_t total = (size_t)n * slots * N;
     const int LK = NS + K;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -157,8 +180,10 @@ __global__ void k_modup(const u64* A, const u64* B, u64* X, int n, int slots, in
         if constexpr (FAST) {
             uint32_t y0[NS], y1[NS];
             int vv = 0;
-            if (fast_prep<NS>(x, ext, y0, y1, vv)) {
-                for (int j = 0; j < K; ++j) dst[(size_t)(NS + j) * N] = fast_eval<NS>(y0, y1, vv, ext, j);
+            if (fast_prep<NS, NS + 1>(x, ext, ft, y0, y1, vv)) {   // the fast path has K = NS + 1 targets
+#pragma unroll
+                for (int j = 0; j < NS + 1; ++j)
+                    dst[(size_t)(NS + j) * N] = fast_eval<NS, NS + 1>(y0, y1, vv, ext, ft, j);
                 continue;
             }
         }
@@ -178,7 +203,8 @@ __device__ __forceinline__ ulonglong2 twist_at(const u64* twist, int p, int f, i
 // leave the tensor untwisted: the first product of each limb, by t, also carries the twist N^-1 psi^-k R.
 template <int NS, int KS, bool FAST>
 __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, ExtDesc eQB, ExtDesc eBQ, const u64* twist, int nP,
-                        const u64* Qinv_b, const u64* bq, int N) {
+                        const u64* Qinv_b, const u64* bq, int N, FastTab<FAST ? NS : 1, FAST ? KS : 1> fq,
+                        FastTab<FAST ? KS : 1, FAST ? NS : 1> fb) {
     const size_t total = (size_t)n * 3 * N;
     constexpr int LK = NS + KS;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -201,7 +227,7 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
             uint32_t r0[NS], r1[NS];
             int vv = 0;
             bool fast = false;
-            if constexpr (FAST) fast = fast_prep<NS>(r, eQB, r0, r1, vv);
+            if constexpr (FAST) fast = fast_prep<NS, KS>(r, eQB, fq, r0, r1, vv);
             u64 v[NS];
             bool neg = false;
             if (!fast) neg = garner<NS>(r, eQB, v);
@@ -212,7 +238,8 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
                 const ulonglong2 f = twist_at(twist, pj, 2, k, N);
                 const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], f.x, f.y, bj);   // [t d]_{b_j}, < 2 b_j
                 u64 rb;
-                if constexpr (FAST) rb = fast ? fast_eval<NS>(r0, r1, vv, eQB, j) : ext_eval<NS, false>(v, neg, eQB, j);
+                if constexpr (FAST)
+                    rb = fast ? fast_eval<NS, KS>(r0, r1, vv, eQB, fq, j) : ext_eval<NS, false>(v, neg, eQB, j);
                 else rb = ext_eval<NS, false>(v, neg, eQB, j);
                 y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
             }
@@ -222,9 +249,9 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
         if constexpr (FAST) {
             uint32_t y0[KS], y1[KS];
             int vy = 0;
-            if (fast_prep<KS>(y, eBQ, y0, y1, vy)) {
+            if (fast_prep<KS, NS>(y, eBQ, fb, y0, y1, vy)) {
 #pragma unroll
-                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS>(y0, y1, vy, eBQ, i);
+                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS, NS>(y0, y1, vy, eBQ, fb, i);
                 continue;
             }
         }
@@ -241,7 +268,7 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
 // Measured at N = 32768, L = 16: mul_relin +10.6%, squarings +12.1%; at L = 8 the one-pass kernel is 1% faster.
 template <int NS, int KS>
 __global__ void __launch_bounds__(256, 2) k_scale_a(const u64* X, u64* Yt, int n, ExtDesc eQB, const u64* twist, int nP,
-                                                    const u64* Qinv_b, const u64* bq, int N) {
+                                                    const u64* Qinv_b, const u64* bq, int N, FastTab<NS, KS> fq) {
     const size_t total = (size_t)n * 3 * N;
     constexpr int LK = NS + KS;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -262,7 +289,7 @@ __global__ void __launch_bounds__(256, 2) k_scale_a(const u64* X, u64* Yt, int n
                 const ulonglong2 f = twist_at(twist, i, 2, k, N);
                 r[i] = shoup_lazy(d[(size_t)i * N], f.x, f.y, eQB.src_q[i]);
             }
-            fast = fast_prep<NS>(r, eQB, r0, r1, vv);
+            fast = fast_prep<NS, KS>(r, eQB, fq, r0, r1, vv);
         }
         if (!fast) {
             // the exact mixed-radix path near the rounding boundary (rare): recompute r from memory
@@ -289,14 +316,15 @@ __global__ void __launch_bounds__(256, 2) k_scale_a(const u64* X, u64* Yt, int n
             const int pj = NS + (nP - 1 - NS - KS) + j;
             const ulonglong2 f = twist_at(twist, pj, 2, k, N);
             const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], f.x, f.y, bj);
-            const u64 rb = fast_eval<NS>(r0, r1, vv, eQB, j);
+            const u64 rb = fast_eval<NS, KS>(r0, r1, vv, eQB, fq, j);
             yo[(size_t)j * N] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);
         }
     }
 }
 
 template <int NS, int KS>
-__global__ void __launch_bounds__(256, 2) k_scale_b(const u64* Yt, u64* C3, int n, ExtDesc eBQ, int N) {
+__global__ void __launch_bounds__(256, 2) k_scale_b(const u64* Yt, u64* C3, int n, ExtDesc eBQ, int N,
+                                                    FastTab<KS, NS> fb) {
     const size_t total = (size_t)n * 3 * N;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -309,9 +337,9 @@ __global__ void __launch_bounds__(256, 2) k_scale_b(const u64* Yt, u64* C3, int 
         u64* o = C3 + cp * (size_t)NS * N + k;
         uint32_t y0[KS], y1[KS];
         int vy = 0;
-        if (fast_prep<KS>(y, eBQ, y0, y1, vy)) {
+        if (fast_prep<KS, NS>(y, eBQ, fb, y0, y1, vy)) {
 #pragma unroll
-            for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS>(y0, y1, vy, eBQ, i);
+            for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS, NS>(y0, y1, vy, eBQ, fb, i);
             continue;
         }
         u64 w[KS];
@@ -525,10 +553,12 @@ __global__ void k_dec_finish_n(const u64* V, const u64* ct, u64* M, int n, ExtDe
 template <int NS>
 int run_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const size_t work = (size_t)n * slots * ctx->N;
-    if (ctx->fast_ext && ctx->ext_QB.fast_ok)
-        LAUNCH((k_modup<NS, true>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
+    if (ctx->fast_ext && ctx->ext_QB.fast_ok && (int)ctx->K == NS + 1)
+        LAUNCH((k_modup<NS, true>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags,
+               fast_tab<NS, NS + 1>(ctx->exth_QB));
     else
-        LAUNCH((k_modup<NS, false>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags);
+        LAUNCH((k_modup<NS, false>), work, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N, ctx->d_flags,
+               FastTab<1, 1>{});
     return BFHE_OK;
 }
 
@@ -540,17 +570,18 @@ int run_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st
     if constexpr (NS >= 10) {
         if (tmp && fast) {
             LAUNCH((k_scale_a<NS, NS + 1>), work, X, tmp, n, ctx->ext_QB, ctx->tab.twist, (int)ctx->nP,
-                   ctx->d_Qinv_b, bq, (int)ctx->N);
-            LAUNCH((k_scale_b<NS, NS + 1>), work, tmp, C3, n, ctx->ext_BQ, (int)ctx->N);
+                   ctx->d_Qinv_b, bq, (int)ctx->N, fast_tab<NS, NS + 1>(ctx->exth_QB));
+            LAUNCH((k_scale_b<NS, NS + 1>), work, tmp, C3, n, ctx->ext_BQ, (int)ctx->N,
+                   fast_tab<NS + 1, NS>(ctx->exth_BQ));
             return BFHE_OK;
         }
     }
     if (fast)
         LAUNCH((k_scale<NS, NS + 1, true>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
-               ctx->d_Qinv_b, bq, (int)ctx->N);
+               ctx->d_Qinv_b, bq, (int)ctx->N, fast_tab<NS, NS + 1>(ctx->exth_QB), fast_tab<NS + 1, NS>(ctx->exth_BQ));
     else
         LAUNCH((k_scale<NS, NS + 1, false>), work, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
-               ctx->d_Qinv_b, bq, (int)ctx->N);
+               ctx->d_Qinv_b, bq, (int)ctx->N, FastTab<1, 1>{}, FastTab<1, 1>{});
     return BFHE_OK;
 }
 

@@ -139,7 +139,7 @@ struct ExtOffsets {
     size_t qhinv, qhinv_s, g_hi, g_lo, c26, dst_qinv, vS;
 };
 
-ExtOffsets build_ext(Arena& ar, const std::vector<u64>& src, const std::vector<u64>& dst) {
+ExtOffsets build_ext(Arena& ar, const std::vector<u64>& src, const std::vector<u64>& dst, ExtHost* host = nullptr) {
     const int n = (int)src.size(), m = (int)dst.size();
     std::vector<u64> ginv(n * n, 0), ginv_s(n * n, 0), hres(n), radix(m * n), radix_s(m * n), smod(m), mu(m);
     for (int i = 0; i < n; ++i) {
@@ -196,6 +196,15 @@ ExtOffsets build_ext(Arena& ar, const std::vector<u64>& src, const std::vector<u
             c26[((size_t)j * n + i) * 2 + 0] = (uint32_t)(cv & 0x3FFFFFFull);
             c26[((size_t)j * n + i) * 2 + 1] = (uint32_t)(cv >> 26);
         }
+    }
+    if (host) {
+        host->n = n;
+        host->m = m;
+        host->c26.assign(c26, c26 + (size_t)m * n * 2);
+        host->qhinv = qhinv;
+        host->qhinv_s = qhinv_s;
+        host->g_hi = g_hi;
+        host->g_lo = g_lo;
     }
     ExtOffsets o;
     o.n = n;
@@ -557,8 +566,8 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     std::vector<u64> Pp(c->primes.begin() + L, c->primes.begin() + L + A);
     std::vector<u64> Bp(c->primes.begin() + L + A, c->primes.begin() + L + A + K);
     std::vector<u64> Tp{t};
-    const ExtOffsets eQB = build_ext(ar, Qp, Bp), eBQ = build_ext(ar, Bp, Qp), ePQ = build_ext(ar, Pp, Qp),
-                     eQt = build_ext(ar, Qp, Tp);
+    const ExtOffsets eQB = build_ext(ar, Qp, Bp, &c->exth_QB), eBQ = build_ext(ar, Bp, Qp, &c->exth_BQ),
+                     ePQ = build_ext(ar, Pp, Qp), eQt = build_ext(ar, Qp, Tp);
 
     // scalar constants
     u64 Qt = 1;
