@@ -354,31 +354,40 @@ __global__ void __launch_bounds__(256, 2) k_scale_b(const u64* Yt, u64* C3, int 
 template <int NA>
 __global__ void k_moddown(const u64* W, const u64* C3, u64* out, int n, int L, ExtDesc ePQ, const u64* Pinv,
                           const u64* qtab, const u64* twist, int N) {
-    const size_t total = (size_t)n * 2 * N;
+    // two consecutive coefficients per thread (N is even, every limb starts 16-byte aligned): 16-byte accesses
+    const size_t half = (size_t)N >> 1;
+    const size_t total = (size_t)n * 2 * half;
     const int QP = L + NA;
+    const ulonglong2* tw2 = reinterpret_cast<const ulonglong2*>(twist);
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const size_t cp = idx / N;
+        const int k = (int)(idx % half) * 2;
+        const size_t cp = idx / half;
         const size_t c = cp >> 1;
         const int comp = (int)(cp & 1);
         const u64* w = W + cp * (size_t)QP * N + k;
-        u64 x[NA], v[NA];
+        u64 x0[NA], x1[NA], v0[NA], v1[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            const ulonglong2 f = twist_at(twist, L + a, 1, k, N);
-            x[a] = shoup_lazy(w[(size_t)(L + a) * N], f.x, f.y, ePQ.src_q[a]);   // < 2 p_a
+            const ulonglong2 ww = *reinterpret_cast<const ulonglong2*>(w + (size_t)(L + a) * N);
+            const ulonglong2* f = tw2 + ((size_t)(L + a) * 3 + 1) * N + k;
+            const ulonglong2 f0 = __ldg(f), f1 = __ldg(f + 1);
+            x0[a] = shoup_lazy(ww.x, f0.x, f0.y, ePQ.src_q[a]);   // < 2 p_a
+            x1[a] = shoup_lazy(ww.y, f1.x, f1.y, ePQ.src_q[a]);
         }
-        const bool neg = garner<NA>(x, ePQ, v);
+        const bool neg0 = garner<NA>(x0, ePQ, v0), neg1 = garner<NA>(x1, ePQ, v1);
         const u64* cin = C3 + (c * 3 + comp) * (size_t)L * N + k;
         u64* o = out + cp * (size_t)L * N + k;
         for (int i = 0; i < L; ++i) {
-            const u64 qi = qtab[i];
-            const ulonglong2 f = twist_at(twist, i, 1, k, N);
-            const u64 wi = shoup_lazy(w[(size_t)i * N], f.x, f.y, qi);   // < 2 q_i
-            const u64 e = ext_eval<NA, false>(v, neg, ePQ, i);
-            const u64 y = shoup(sub_mod(wi, e, qi), Pinv[i], Pinv[L + i], qi);
-            o[(size_t)i * N] = add_mod(cin[(size_t)i * N], y, qi);
+            const u64 qi = qtab[i], pw = Pinv[i], pws = Pinv[L + i];
+            const ulonglong2* f = tw2 + ((size_t)i * 3 + 1) * N + k;
+            const ulonglong2 f0 = __ldg(f), f1 = __ldg(f + 1);
+            const ulonglong2 ww = *reinterpret_cast<const ulonglong2*>(w + (size_t)i * N);
+            const ulonglong2 cc = *reinterpret_cast<const ulonglong2*>(cin + (size_t)i * N);
+            const u64 w0 = shoup_lazy(ww.x, f0.x, f0.y, qi), w1 = shoup_lazy(ww.y, f1.x, f1.y, qi);   // < 2 q_i
+            const u64 y0 = shoup(sub_mod(w0, ext_eval<NA, false>(v0, neg0, ePQ, i), qi), pw, pws, qi);
+            const u64 y1 = shoup(sub_mod(w1, ext_eval<NA, false>(v1, neg1, ePQ, i), qi), pw, pws, qi);
+            *reinterpret_cast<ulonglong2*>(o + (size_t)i * N) = make_ulonglong2(add_mod(cc.x, y0, qi), add_mod(cc.y, y1, qi));
         }
     }
 }
@@ -640,7 +649,7 @@ int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, i
     const double A_ = ctx->alpha;
     // work: the rounding division by P, plus the twist the inverse transform left to this kernel
     ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_ + ctx->L + A_));
-    const size_t work = (size_t)n * 2 * ctx->N;
+    const size_t work = (size_t)n * ctx->N;   // two coefficients per thread
     if (ctx->alpha == 1)
         LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, ctx->tab.twist,
                (int)ctx->N);
