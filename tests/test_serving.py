@@ -242,8 +242,11 @@ def test_gpu_result_is_the_same_alone_and_in_the_mix():
         slots = b.slots(r)
         ctx = b.ctx[r.N]
         if r.kind == "bridge":
-            # the library's own conversion (Listing 8, select mode) of the same encrypted input, word for word
-            want = ctx.mod_to_bits(b.encrypt(r), r.s, 0, (1 << r.s) - 1, bfhe.SELECT)
+            # the library's own conversion (Listing 8, select mode) of the same encrypted input, word for word;
+            # on the backend's stream, which the encryption was launched on
+            with torch.cuda.stream(b.stream[r.N]):
+                want = ctx.mod_to_bits(b.encrypt(r), r.s, 0, (1 << r.s) - 1, bfhe.SELECT)
+            b.synchronize()
             assert torch.equal(r.result, want)
             continue
         # a chain decrypts to the slot values raised to 2^depth
