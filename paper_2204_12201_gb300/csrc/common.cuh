@@ -145,6 +145,7 @@ struct PrimeTab {
     const u64* qinv;     // -q^-1 mod 2^64
     const u64* mu;       // floor(2^64 / q)
     const u64* tw;       // [nP][N][2] (psi^brv(k), Shoup companion)      forward twiddles
+    const u64* twl;      // [nP][3][N][2] the same, stages b < le regrouped per le = 3, 4, 5 (forward last pass)
     const u64* itw;      // [nP][N][2] inverse (DIT) twiddles: entry 2^b + j = omega^-(N/2^(b+1)) j, omega = psi^2
     const u64* twist;    // [nP][3][N][2] output twist N^-1 psi^-m (plain; times R = 2^64; times t R), mod q
 };
@@ -215,7 +216,7 @@ struct bfhe_ctx {
     // launch timing (measurement only): pending (class, start, stop) event triples
     struct ProfRec {
         int cls;
-        double work;
+        double work, bytes;
         cudaEvent_t a, b;
     };
     mutable bool prof_on = false;
@@ -254,13 +255,15 @@ size_t mul_scratch_bytes(const bfhe_ctx* ctx, size_t n);
 
 // RAII bracket of one launcher's kernels by CUDA events when profiling is on
 // (work = the launch's algorithmic 64-bit modular multiplies)
+// work: algorithmic modmuls of the launch; bytes: its algorithmic DRAM bytes (each operand read and each
+// result written once; tables that stay in L2 not counted)
 struct ProfScope {
     const bfhe_ctx* c;
     int cls;
-    double work;
+    double work, bytes;
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
-    ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w);
+    ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w, double by);
     ~ProfScope();
 };
 

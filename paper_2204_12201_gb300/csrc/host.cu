@@ -306,7 +306,8 @@ static cudaEvent_t take_event(const bfhe_ctx* c) {
     return e;
 }
 
-ProfScope::ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w) : c(ctx), cls(k), work(w), st(s) {
+ProfScope::ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w, double by)
+    : c(ctx), cls(k), work(w), bytes(by), st(s) {
     if (!c->prof_on || c->capturing) return;
     a = take_event(c);
     b = take_event(c);
@@ -316,7 +317,7 @@ ProfScope::ProfScope(const bfhe_ctx* ctx, int k, cudaStream_t s, double w) : c(c
 ProfScope::~ProfScope() {
     if (!a || !b) return;
     cudaEventRecord(b, st);
-    c->prof_pending.push_back(bfhe_ctx::ProfRec{cls, work, a, b});
+    c->prof_pending.push_back(bfhe_ctx::ProfRec{cls, work, bytes, a, b});
 }
 
 extern "C" int bfhe_profile(bfhe_ctx* ctx, int enable) {
@@ -325,12 +326,14 @@ extern "C" int bfhe_profile(bfhe_ctx* ctx, int enable) {
     return BFHE_OK;
 }
 
-extern "C" int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out) {
+extern "C" int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out,
+                                 double* bytes_out) {
     if (!ctx || !ms_out || !launches_out) return set_error(BFHE_EINVAL, "null argument");
     for (int k = 0; k < BFHE_K_COUNT; ++k) {
         ms_out[k] = 0;
         launches_out[k] = 0;
         if (work_out) work_out[k] = 0;
+        if (bytes_out) bytes_out[k] = 0;
     }
     int rc = BFHE_OK;
     for (auto& r : ctx->prof_pending) {
@@ -342,6 +345,7 @@ extern "C" int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launch
             ms_out[r.cls] += ms;
             launches_out[r.cls] += 1;
             if (work_out) work_out[r.cls] += r.work;
+            if (bytes_out) bytes_out[r.cls] += r.bytes;
         }
         ctx->prof_pool.push_back(r.a);
         ctx->prof_pool.push_back(r.b);
@@ -502,6 +506,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     Arena ar;
     std::vector<u64> qv(c->primes), qinv(nP), mu(nP), R2(nP);
     std::vector<u64> tw((size_t)nP * N * 2), itw((size_t)nP * N * 2), twist((size_t)nP * 3 * N * 2);
+    std::vector<u64> twl((size_t)nP * 3 * N * 2);
     for (uint32_t p = 0; p < nP; ++p) {
         const u64 q = c->primes[p];
         if (p == nP - 1 && !batching) {
@@ -530,6 +535,26 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
             tw[o] = pw[c->brv[k]];
             tw[o + 1] = shoup_of(tw[o], q);
         }
+        // the forward's last pass (E = 2^le words per thread, stages on bits b < le): the entries of stage b,
+        // [N >> (b+1), N >> b), regrouped so that lanes of a warp read consecutive entries: thread tg's g-th
+        // twiddle (standard entry (N >> (b+1)) + tg B + g, B = E >> (b+1)) at (N >> (b+1)) + g (N / E) + tg
+        for (uint32_t le = 3; le <= 5; ++le) {
+            const size_t o = ((size_t)p * 3 + (le - 3)) * N * 2;
+            const size_t ot = (size_t)p * N * 2;
+            for (uint32_t k = 0; k < (N >> le); ++k) {
+                twl[o + 2 * k] = tw[ot + 2 * k];
+                twl[o + 2 * k + 1] = tw[ot + 2 * k + 1];
+            }
+            const uint32_t T = N >> le;
+            for (uint32_t b = 0; b < le; ++b) {
+                const uint32_t lo = N >> (b + 1), B = (1u << le) >> (b + 1);
+                for (uint32_t r = 0; r < lo; ++r) {
+                    const uint32_t d = lo + (r % B) * T + r / B;
+                    twl[o + 2 * (size_t)d] = tw[ot + 2 * (size_t)(lo + r)];
+                    twl[o + 2 * (size_t)d + 1] = tw[ot + 2 * (size_t)(lo + r) + 1];
+                }
+            }
+        }
         // inverse DIT: entry 2^b + j (j < 2^b) = omega^-((N >> (b+1)) j) = psi^-(2 (N >> (b+1)) j)
         itw[(size_t)p * N * 2] = 1;
         itw[(size_t)p * N * 2 + 1] = shoup_of(1, q);
@@ -555,7 +580,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
         }
     }
     const size_t o_q = ar.add(qv), o_qinv = ar.add(qinv), o_mu = ar.add(mu), o_R2 = ar.add(R2);
-    const size_t o_tw = ar.add(tw), o_itw = ar.add(itw), o_twist = ar.add(twist);
+    const size_t o_tw = ar.add(tw), o_twl = ar.add(twl), o_itw = ar.add(itw), o_twist = ar.add(twist);
     std::vector<u64> brv_packed((N + 1) / 2);
     for (uint32_t k = 0; k < N; k += 2)
         brv_packed[k / 2] = (u64)c->brv[k] | ((u64)(k + 1 < N ? c->brv[k + 1] : 0) << 32);
@@ -620,6 +645,7 @@ extern "C" int bfhe_ctx_create(const bfhe_params* prm, int device, bfhe_ctx** ou
     c->tab.qinv = base + o_qinv;
     c->tab.mu = base + o_mu;
     c->tab.tw = base + o_tw;
+    c->tab.twl = base + o_twl;
     c->tab.itw = base + o_itw;
     c->tab.twist = base + o_twist;
     c->d_R2 = base + o_R2;

@@ -12,7 +12,8 @@
 // bit-reversed input with the same reduction-free butterfly, then one twist
 // product by N^-1 psi^-m per word (times R = 2^64 when the inputs carry a
 // Montgomery factor), which also makes the output canonical.  Twiddles are
-// stored as (w, Shoup(w)) pairs and fetched as one 16-byte load.
+// stored as (w, Shoup(w)) pairs and fetched as one 16-byte load; the forward's
+// last pass reads a copy regrouped so that a warp's loads are contiguous.
 //
 // One CTA transforms a block of M = 2^LOG_M words of a limb held in shared
 // memory; each thread keeps E = 2^LOG_E words in registers and runs up to
@@ -85,8 +86,13 @@ __device__ __forceinline__ LimbPtrs limb_ptrs(const NttArgs& a, int bx) {
 }
 
 // ---------------------------------------------------------------- forward stages
-template <int LOG_E, int W_LO, int HI, int LO>
-__device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw, u64 q) {
+// The last pass (W_LO = 0: E consecutive words per thread) takes its twiddles from the regrouped table:
+// twc is this thread's column there, and its g-th twiddle of stage b sits (N >> (b+1)) + g (N / E) entries
+// further, so lanes read consecutive 16-byte entries (the standard table gives each lane its own run of
+// E >> (b+1) entries: 32 sectors per warp load instead of 16 contiguous).
+template <int LOG_N, int LOG_E, int W_LO, int HI, int LO>
+__device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const ulonglong2* __restrict__ tw,
+                                           const ulonglong2* __restrict__ twc, u64 q) {
     constexpr int E = 1 << LOG_E;
     const u64 q4 = 4 * q, nq = 0 - q;
 #pragma unroll
@@ -96,7 +102,8 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
         const u64 base = jb >> (b + 1);
 #pragma unroll
         for (int g = 0; g < (E >> (h + 1)); ++g) {
-            const ulonglong2 wp = __ldg(tw + base + g);
+            const ulonglong2 wp = W_LO == 0 ? __ldg(twc + ((1 << LOG_N) >> (b + 1)) + g * (1 << (LOG_N - LOG_E)))
+                                            : __ldg(tw + base + g);
 #pragma unroll
             for (int r = 0; r < (1 << h); ++r) {
                 const int e = (g << (h + 1)) | r;
@@ -114,7 +121,7 @@ __device__ __forceinline__ void fwd_stages(u64 (&x)[1 << LOG_E], u64 jb, const u
 // outermost stage (twiddle psi^brv(1)) to the pairs (j, j + M) it reads.
 template <int LOG_M, int LOG_E, int P, bool TOP, bool LAZY>
 __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid, u64 jglob, const ulonglong2* tw,
-                                         u64 q, u64 mu, const u64* in, u64* out, int half) {
+                                         const ulonglong2* twl, u64 q, u64 mu, const u64* in, u64* out, int half) {
     constexpr int E = 1 << LOG_E;
     constexpr int M = 1 << LOG_M;
     constexpr int NPASS = (LOG_M + LOG_E - 1) / LOG_E;
@@ -143,12 +150,15 @@ __device__ __forceinline__ void fwd_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = sm[pb + poff<W_LO>(e)];
     }
-    fwd_stages<LOG_E, W_LO, HI, LO>(x, jglob + base, tw, q);
+    constexpr int LOG_N = TOP ? LOG_M + 1 : LOG_M;
+    // thread index over the whole limb (last pass): (jglob - N + base) / E
+    const ulonglong2* twc = W_LO == 0 ? twl + ((((u64)half << LOG_M) + base) >> LOG_E) : twl;
+    fwd_stages<LOG_N, LOG_E, W_LO, HI, LO>(x, jglob + base, tw, twc, q);
     if constexpr (P + 1 < NPASS) {
 #pragma unroll
         for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
         __syncthreads();
-        fwd_pass<LOG_M, LOG_E, P + 1, TOP, LAZY>(x, sm, tid, jglob, tw, q, mu, in, out, half);
+        fwd_pass<LOG_M, LOG_E, P + 1, TOP, LAZY>(x, sm, tid, jglob, tw, twl, q, mu, in, out, half);
     } else {
         // W_LO == 0 here: E consecutive words per thread; values < 64q -> canonical unless the
         // consumer takes lazy words (Montgomery products of operands < 64q, q < 2^50)
@@ -169,11 +179,12 @@ __global__ void __launch_bounds__(1 << (LOG_M - LOG_E), (LOG_M < 14 && LOG_M - L
     const int half = blockIdx.y;
     const u64 q = a.tab.q[lp.p], mu = a.tab.mu[lp.p];
     const ulonglong2* tw = reinterpret_cast<const ulonglong2*>(a.tab.tw) + (size_t)lp.p * a.N;
+    const ulonglong2* twl = reinterpret_cast<const ulonglong2*>(a.tab.twl) + ((size_t)lp.p * 3 + (LOG_E - 3)) * a.N;
     const u64 jglob = (u64)a.N + ((u64)half << LOG_M);
     const u64* in = TOP ? lp.in : lp.in + ((size_t)half << LOG_M);
     u64 x[1 << LOG_E];
-    fwd_pass<LOG_M, LOG_E, 0, TOP, LAZY>(x, sm, threadIdx.x, jglob, tw, q, mu, in, lp.out + ((size_t)half << LOG_M),
-                                         half);
+    fwd_pass<LOG_M, LOG_E, 0, TOP, LAZY>(x, sm, threadIdx.x, jglob, tw, twl, q, mu, in,
+                                         lp.out + ((size_t)half << LOG_M), half);
 }
 
 // ---------------------------------------------------------------- inverse stages
@@ -467,7 +478,8 @@ int run_inv_any(const NttArgs& a, int blocks, cudaStream_t st, bool split, int o
 int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, cudaStream_t st,
                    int lazy_out) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
-    ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
+    ProfScope ps(ctx, BFHE_K_NTT_FWD, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN,
+                 16.0 * n_polys * n_limbs * ctx->N);
     int log_m, log_e;
     ntt_config((int)ctx->logN, 0, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, 0, lazy_out && ctx->prime_bits <= 50 ? 1 : 0);
@@ -487,7 +499,8 @@ int launch_ntt_fwd(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, Limb
 int launch_ntt_inv(const bfhe_ctx* ctx, NttIO io, int n_polys, int n_limbs, LimbMap map, int mont,
                    cudaStream_t st, int lazy_out) {
     if (n_polys <= 0 || n_limbs <= 0) return BFHE_OK;
-    ProfScope ps(ctx, BFHE_K_NTT_INV, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN);
+    ProfScope ps(ctx, BFHE_K_NTT_INV, st, (double)n_polys * n_limbs * (ctx->N / 2) * ctx->logN,
+                 16.0 * n_polys * n_limbs * ctx->N);
     int log_m, log_e;
     ntt_config((int)ctx->logN, 1, &log_m, &log_e);
     NttArgs a = make_args(ctx, io, n_limbs, map, mont, lazy_out);
