@@ -105,6 +105,19 @@ def alu_peak_modmul_per_s(sms, mhz):
     return sms * 64.0 * mhz * 1e6 / 16.0
 
 
+def kernel_rooflines(prof, alu_peak, hbm_gbs):
+    """Per kernel class: its roofline time is the slower of the algorithmic modmuls at the integer-pipe peak
+    and the algorithmic DRAM bytes at the measured copy bandwidth; frac = that time / the measured time."""
+    out = {}
+    for k, (ms, _, work, nbytes) in prof.items():
+        if ms <= 0:
+            continue
+        t_alu, t_hbm = work / alu_peak, nbytes / (hbm_gbs * 1e9)
+        out[k] = {"bound": "alu" if t_alu >= t_hbm else "hbm", "frac": round(max(t_alu, t_hbm) / (ms / 1e3), 3),
+                  "alu_frac": round(t_alu / (ms / 1e3), 3), "hbm_frac": round(t_hbm / (ms / 1e3), 3)}
+    return out
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
 
@@ -562,7 +575,7 @@ def main():
     props = torch.cuda.get_device_properties(local)
     peak = alu_peak_modmul_per_s(props.multi_processor_count, peaks.get("sm_max_mhz", 2070.0))
     dom = max(prof, key=lambda k: prof[k][0])
-    d_ms, d_launch, d_work = prof[dom]
+    d_ms, d_launch, d_work, _ = prof[dom]
     achieved = d_work / (d_ms / 1e3)
     traffic = None
     if dom.startswith("ntt"):
@@ -583,7 +596,8 @@ def main():
                 "avg_launch_ms": d_ms / max(1, d_launch), "launches": d_launch,
                 "kernel_share": {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 3)
                                  for k, v in prof.items()},
-                "kernel_alu_frac": {k: round(v[2] / (v[0] / 1e3) / peak, 3) for k, v in prof.items() if v[0] > 0}}
+                "kernel_alu_frac": {k: round(v[2] / (v[0] / 1e3) / peak, 3) for k, v in prof.items() if v[0] > 0},
+                "kernel_roofline": kernel_rooflines(prof, peak, peaks.get("hbm_gbs", 6800.0))}
 
     ext = {} if args.no_extras else extras(torch, bfhe, circuits, ctx)
     # what the headline counts: mostly Fermat squarings and paper-mode ANDs of the bridge

@@ -363,18 +363,25 @@ int bfhe_ntt_config(uint32_t logN, int inverse, uint32_t log_m, uint32_t log_e, 
 /* Measurement support.  While profiling is on, every launch of the kernel
  * classes below is bracketed by CUDA events on its own stream;
  * bfhe_profile_read synchronises on the last event and returns, per class,
- * the summed device time in ms, the number of launches and (work_out, may
- * be NULL) the algorithmic 64-bit modular multiplies those launches
- * performed (arrays of BFHE_K_COUNT), then clears the record.  Modmul
- * counts: NTT (N/2) log2 N per limb; modup per coefficient L(L-1)/2 +
- * K(L-1); scale per coefficient of each of 3 polys 2L + 3K + L(L-1)/2 +
- * K(L-1) + K(K-1)/2 + L(K-1) (both the exact algorithm's count, also when
- * the fast extension ran); tensor 4 per limb word; inner 2L per word of
- * the Q u P limbs; moddown per coefficient alpha(alpha-1)/2 + L alpha. */
+ * the summed device time in ms, the number of launches, (work_out, may be
+ * NULL) the algorithmic 64-bit modular multiplies those launches performed
+ * and (bytes_out, may be NULL) their algorithmic DRAM bytes, every operand
+ * read and every result written once (arrays of BFHE_K_COUNT), then clears
+ * the record.  Modmul counts: NTT (N/2) log2 N per limb; modup per
+ * coefficient L(L-1)/2 + K(L-1); scale per coefficient of each of 3 polys
+ * 2L + 3K + L(L-1)/2 + K(L-1) + K(K-1)/2 + L(K-1) (both the exact
+ * algorithm's count, also when the fast extension ran); tensor 4 per limb
+ * word; inner 2L per word of the Q u P limbs; moddown per coefficient of
+ * each of 2 polys alpha(alpha-1)/2 + L alpha + L + alpha (with the inverse
+ * transform's twist).  Bytes: NTT 16N per limb; modup 8(2L + K) per
+ * coefficient of an input poly; scale 8(2L + K) per coefficient of each of
+ * 3 polys; tensor 56 (squaring 40) per limb word of Q u B; inner 8(L + 2)
+ * per word of Q u P per ciphertext plus the key's 16L once per launch;
+ * moddown 8(3L + alpha) per coefficient of each of 2 polys. */
 enum { BFHE_K_NTT_FWD = 0, BFHE_K_NTT_INV = 1, BFHE_K_MODUP = 2, BFHE_K_TENSOR = 3, BFHE_K_SCALE = 4,
        BFHE_K_INNER = 5, BFHE_K_MODDOWN = 6, BFHE_K_COUNT = 7 };
 int bfhe_profile(bfhe_ctx* ctx, int enable);
-int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out);
+int bfhe_profile_read(bfhe_ctx* ctx, double* ms_out, uint64_t* launches_out, double* work_out, double* bytes_out);
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t bfhe_launch_count(void);

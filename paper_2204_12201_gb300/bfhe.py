@@ -70,7 +70,7 @@ def load():
         "bfhe_op_counts": (I, [P, P, I]),
         "bfhe_ntt": (I, [P, P, S, U32, I, P]),
         "bfhe_profile": (I, [P, I]),
-        "bfhe_profile_read": (I, [P, P, P, P]),
+        "bfhe_profile_read": (I, [P, P, P, P, P]),
         "bfhe_probe_modmul": (I, [I, U32, P, P]),
         "bfhe_launch_count": (ctypes.c_uint64, []),
         "bfhe_set_scratch_budget": (I, [S]),
@@ -370,12 +370,13 @@ class Context:
         _check(self.lib.bfhe_profile(self.h, int(enable)))
 
     def profile_read(self):
-        """{class: (ms, launches, modmuls)} since the last read (synchronises)."""
+        """{class: (ms, launches, modmuls, algorithmic DRAM bytes)} since the last read (synchronises)."""
         ms = (ctypes.c_double * len(KERNEL_CLASSES))()
         cnt = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         work = (ctypes.c_double * len(KERNEL_CLASSES))()
-        _check(self.lib.bfhe_profile_read(self.h, ms, cnt, work))
-        return {k: (ms[i], int(cnt[i]), work[i]) for i, k in enumerate(KERNEL_CLASSES)}
+        nbytes = (ctypes.c_double * len(KERNEL_CLASSES))()
+        _check(self.lib.bfhe_profile_read(self.h, ms, cnt, work, nbytes))
+        return {k: (ms[i], int(cnt[i]), work[i], nbytes[i]) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def probe_modmul(device=0, iters=1 << 14):

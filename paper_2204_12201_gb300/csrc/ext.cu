@@ -625,7 +625,9 @@ int run_dec_finish(const bfhe_ctx* ctx, const u64* V, const u64* ct, u64* M, int
 
 int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n, int slots, cudaStream_t st) {
     const double L_ = ctx->L, K_ = ctx->K;
-    ProfScope ps(ctx, BFHE_K_MODUP, st, (double)slots * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)));
+    // L limbs read, L + K written per coefficient of each input poly
+    ProfScope ps(ctx, BFHE_K_MODUP, st, (double)slots * n * ctx->N * (L_ * (L_ - 1) / 2 + K_ * (L_ - 1)),
+                 8.0 * slots * n * ctx->N * (2 * L_ + K_));
     SWITCH_L(ctx->L, run_modup, ctx, A, B, X, n, slots, st)
     if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
     LAUNCH(k_modup_n, (size_t)n * slots * ctx->N, A, B, X, n, slots, (int)ctx->K, ctx->ext_QB, (int)ctx->N,
@@ -636,8 +638,10 @@ int launch_modup(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* X, int n,
 int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t st, u64* tmp) {
     if (ctx->K != ctx->L + 1) return set_error(BFHE_EINVAL, "auxiliary base must have L+1 primes");
     const double L_ = ctx->L, K_ = ctx->K;
+    // per coefficient of each of 3 polys: L + K limbs read, L written
     ProfScope ps(ctx, BFHE_K_SCALE, st,
-                 3.0 * n * ctx->N * (2 * L_ + 3 * K_ + L_ * (L_ - 1) / 2 + K_ * (L_ - 1) + K_ * (K_ - 1) / 2 + L_ * (K_ - 1)));
+                 3.0 * n * ctx->N * (2 * L_ + 3 * K_ + L_ * (L_ - 1) / 2 + K_ * (L_ - 1) + K_ * (K_ - 1) / 2 + L_ * (K_ - 1)),
+                 24.0 * n * ctx->N * (2 * L_ + K_));
     SWITCH_L(ctx->L, run_scale, ctx, X, C3, n, st, tmp)
     if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
     LAUNCH(k_scale_n, (size_t)n * 3 * ctx->N, X, C3, n, ctx->ext_QB, ctx->ext_BQ, ctx->tab.twist, (int)ctx->nP,
@@ -648,7 +652,9 @@ int launch_scale(const bfhe_ctx* ctx, const u64* X, u64* C3, int n, cudaStream_t
 int launch_moddown(const bfhe_ctx* ctx, const u64* W, const u64* C3, u64* out, int n, cudaStream_t st) {
     const double A_ = ctx->alpha;
     // work: the rounding division by P, plus the twist the inverse transform left to this kernel
-    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_ + ctx->L + A_));
+    // per coefficient of each of 2 polys: L + alpha words of W and L of C3 read, L written
+    ProfScope ps(ctx, BFHE_K_MODDOWN, st, 2.0 * n * ctx->N * (A_ * (A_ - 1) / 2 + ctx->L * A_ + ctx->L + A_),
+                 16.0 * n * ctx->N * (3.0 * ctx->L + A_));
     const size_t work = (size_t)n * ctx->N;   // two coefficients per thread
     if (ctx->alpha == 1)
         LAUNCH(k_moddown<1>, work, W, C3, out, n, (int)ctx->L, ctx->ext_PQ, ctx->d_Pinv_q, ctx->tab.q, ctx->tab.twist,

@@ -570,7 +570,9 @@ int launch_pointwise(const bfhe_ctx* ctx, const u64* A, const u64* B, u64* out, 
 }
 
 int launch_tensor(const bfhe_ctx* ctx, u64* X, int n, int square, cudaStream_t st) {
-    ProfScope ps(ctx, BFHE_K_TENSOR, st, 4.0 * n * (ctx->L + ctx->K) * ctx->N);
+    // per word of Q u B: 4 read, 3 written (squaring: 2 read)
+    ProfScope ps(ctx, BFHE_K_TENSOR, st, 4.0 * n * (ctx->L + ctx->K) * ctx->N,
+                 (square ? 40.0 : 56.0) * n * (ctx->L + ctx->K) * ctx->N);
     const int LK = (int)(ctx->L + ctx->K);
     if (square)
         LAUNCH(k_tensor_sq, (size_t)n * LK * ctx->N / 2, X, n, LK, ctx->mapQB(), ctx->tab, (int)ctx->N);
@@ -610,7 +612,9 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
     }
 
 int launch_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st) {
-    ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N);
+    // per word of Q u P: L digits read and 2 words written per ciphertext, the key's 2L words once
+    ProfScope ps(ctx, BFHE_K_INNER, st, 2.0 * ctx->L * n * (ctx->L + ctx->alpha) * ctx->N,
+                 8.0 * (ctx->L + ctx->alpha) * ctx->N * ((double)n * (ctx->L + 2) + 2.0 * ctx->L));
     SWITCH_L(ctx->L, run_inner, ctx, Dg, W, n, st)
     if (ctx->L > BFHE_MAX_L) return set_error(BFHE_EINVAL, "unsupported number of data primes");
     const int QP = (int)(ctx->L + ctx->alpha);

@@ -79,3 +79,18 @@ def test_traffic_figure_follows_the_profiled_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench.os.path, "abspath", lambda p: str(tmp_path / "bench.py"))
     assert bench.ntt_traffic_per_limb("k_ntt_fwd") is None
     assert bench.ntt_traffic_per_limb("k_other") is None
+
+
+def test_kernel_roofline_takes_the_slower_bound():
+    """Per class the roofline time is max(modmuls / ALU peak, bytes / HBM peak); frac = that / measured."""
+    sys.path.insert(0, ROOT)
+    import bench
+    alu, gbs = 1e12, 5000.0
+    prof = {"ntt_fwd": (2.0, 3, 1.5e9, 1e9),        # ALU 1.5 ms, HBM 0.2 ms -> alu, 0.75
+            "moddown": (1.0, 1, 1e8, 4e9),          # ALU 0.1 ms, HBM 0.8 ms -> hbm, 0.8
+            "tensor": (0.0, 0, 0.0, 0.0)}           # not launched: absent
+    r = bench.kernel_rooflines(prof, alu, gbs)
+    assert set(r) == {"ntt_fwd", "moddown"}
+    assert r["ntt_fwd"]["bound"] == "alu" and abs(r["ntt_fwd"]["frac"] - 0.75) < 1e-9
+    assert r["moddown"]["bound"] == "hbm" and abs(r["moddown"]["frac"] - 0.8) < 1e-9
+    assert abs(r["moddown"]["alu_frac"] - 0.1) < 1e-9 and abs(r["ntt_fwd"]["hbm_frac"] - 0.1) < 1e-9
