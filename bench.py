@@ -600,6 +600,10 @@ def main():
                 "kernel_roofline": kernel_rooflines(prof, peak, peaks.get("hbm_gbs", 6800.0))}
 
     ext = {} if args.no_extras else extras(torch, bfhe, circuits, ctx)
+    if ext.get("modmul_probe_per_s"):
+        # the same rate against the library's own measured Shoup-product probe (all SMs), the other ALU peak
+        roofline["probe_modmul_per_s"] = ext["modmul_probe_per_s"]
+        roofline["frac_of_probe"] = achieved / ext["modmul_probe_per_s"]
     # what the headline counts: mostly Fermat squarings and paper-mode ANDs of the bridge
     e = WL["t"] - 1
     chains = N_CLASSES * (1 << S_BITS)

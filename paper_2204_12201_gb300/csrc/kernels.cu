@@ -174,16 +174,33 @@ __global__ void k_tensor_sq(u64* X, int n, int LK, LimbMap map, PrimeTab tab, in
     }
 }
 
+// z = sl + sm 2^28 + sh 2^56 as a 128-bit (hi, lo)
+__device__ __forceinline__ void join28(u64 sl, u64 sm, u64 sh, u64& hi, u64& lo) {
+    const u64 mlo = sm << 28, hlo = sh << 56;
+    u64 r = sl + mlo;
+    u64 c = r < mlo ? 1ull : 0ull;
+    lo = r + hlo;
+    c += lo < hlo ? 1ull : 0ull;
+    hi = (sm >> 36) + (sh >> 8) + c;
+}
+
 // key-switch inner product: W[c][comp][k] = sum_j Dg[c][j][k] * rlk[j][comp][k]  (REDC).
 // A thread owns one word (k, coefficient) of Q u P: it keeps the 2L key words of that word in
 // registers and walks a group of ciphertexts, so the key is read once per group.  Up to 8 data primes
 // the digits of the next two ciphertexts are in flight while the current one is accumulated; above 8
 // there is no look-ahead, so that two CTAs of 256 threads still fit an SM (at 16 primes: 166 -> 128
 // registers, +3% mul_relin at N = 32768).
-template <int L>
+// SPLIT (every prime below 2^50, so digits < 64q < 2^56 and key words < 2^50): each operand is cut at bit
+// 28, a = ah 2^28 + al, b = bh 2^28 + bl (al, ah, bl < 2^28, bh < 2^22), and the three partial sums
+// sum al bl, sum (al bh + ah bl), sum ah bh (weights 1, 2^28, 2^56) are 32 x 32 -> 64-bit multiply-adds into
+// 64-bit accumulators: below 16 (2^56 + 2^56) = 2^61 for up to 16 terms, so none overflows; they are joined
+// into the 128-bit sum once per output.  Otherwise each term is a full 64 x 64 -> 128-bit product.
+template <int L, bool SPLIT>
 __global__ void __launch_bounds__(256, 2) k_inner(const u64* Dg, const u64* rlk, u64* W, int n, int QP,
                                                               int cpg, PrimeTab tab, int N) {
+    static_assert(!SPLIT || L <= 16, "the split sums are bounded for at most 16 terms");
     constexpr int D = L <= 8 ? 2 : 0;
+    constexpr uint32_t M28 = (1u << 28) - 1;
     const size_t plane = (size_t)QP * N;
     const int groups = (n + cpg - 1) / cpg;
     const size_t total = plane * groups;
@@ -193,11 +210,15 @@ __global__ void __launch_bounds__(256, 2) k_inner(const u64* Dg, const u64* rlk,
         const int grp = (int)(idx / plane);
         const int k = (int)(off / N);
         const u64 q = tab.q[k], qinv = tab.qinv[k];
-        u64 k0[L], k1[L];
+        u64 k0[L], k1[L];   // SPLIT: (bh << 32) | bl
 #pragma unroll
         for (int j = 0; j < L; ++j) {
             k0[j] = rlk[((size_t)j * 2 + 0) * plane + off];
             k1[j] = rlk[((size_t)j * 2 + 1) * plane + off];
+            if constexpr (SPLIT) {
+                k0[j] = ((k0[j] >> 28) << 32) | ((uint32_t)k0[j] & M28);
+                k1[j] = ((k1[j] >> 28) << 32) | ((uint32_t)k1[j] & M28);
+            }
         }
         const int c0 = grp * cpg, c_end = min(n, (grp + 1) * cpg);
         u64 buf[D + 1][L];
@@ -216,10 +237,30 @@ __global__ void __launch_bounds__(256, 2) k_inner(const u64* Dg, const u64* rlk,
                 for (int j = 0; j < L; ++j) buf[D][j] = d[(size_t)j * plane];
             }
             u64 h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+            if constexpr (SPLIT) {
+                u64 s0l = 0, s0m = 0, s0h = 0, s1l = 0, s1m = 0, s1h = 0;
 #pragma unroll
-            for (int j = 0; j < L; ++j) {
-                mac128(h0, l0, buf[0][j], k0[j]);
-                mac128(h1, l1, buf[0][j], k1[j]);
+                for (int j = 0; j < L; ++j) {
+                    const uint32_t al = (uint32_t)buf[0][j] & M28, ah = (uint32_t)(buf[0][j] >> 28);
+                    const uint32_t b0l = (uint32_t)k0[j], b0h = (uint32_t)(k0[j] >> 32);
+                    const uint32_t b1l = (uint32_t)k1[j], b1h = (uint32_t)(k1[j] >> 32);
+                    s0l += (u64)al * b0l;
+                    s0m += (u64)al * b0h;
+                    s0m += (u64)ah * b0l;
+                    s0h += (u64)ah * b0h;
+                    s1l += (u64)al * b1l;
+                    s1m += (u64)al * b1h;
+                    s1m += (u64)ah * b1l;
+                    s1h += (u64)ah * b1h;
+                }
+                join28(s0l, s0m, s0h, h0, l0);
+                join28(s1l, s1m, s1h, h1, l1);
+            } else {
+#pragma unroll
+                for (int j = 0; j < L; ++j) {
+                    mac128(h0, l0, buf[0][j], k0[j]);
+                    mac128(h1, l1, buf[0][j], k1[j]);
+                }
             }
             W[((size_t)c * 2 + 0) * plane + off] = redc(h0, l0, q, qinv);
             W[((size_t)c * 2 + 1) * plane + off] = redc(h1, l1, q, qinv);
@@ -586,7 +627,10 @@ int run_inner(const bfhe_ctx* ctx, const u64* Dg, u64* W, int n, cudaStream_t st
     const int QP = (int)(ctx->L + ctx->alpha);
     const int cpg = n < 4 ? 1 : (n + 3) / 4;   // four groups: enough threads, key read four times
     const size_t work = (size_t)QP * ctx->N * ((n + cpg - 1) / cpg);
-    LAUNCH(k_inner<L>, work, Dg, ctx->d_rlk_ntt, W, n, QP, cpg, ctx->tab, (int)ctx->N);
+    if (ctx->prime_bits <= 50)   // digits below 64q < 2^56 (lazy transforms), key words below 2^50
+        LAUNCH((k_inner<L, true>), work, Dg, ctx->d_rlk_ntt, W, n, QP, cpg, ctx->tab, (int)ctx->N);
+    else
+        LAUNCH((k_inner<L, false>), work, Dg, ctx->d_rlk_ntt, W, n, QP, cpg, ctx->tab, (int)ctx->N);
     return BFHE_OK;
 }
 
