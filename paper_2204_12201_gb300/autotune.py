@@ -18,7 +18,9 @@ from . import bfhe
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 # ring degree -> (data primes, special primes, batch of the shape search): the workloads' parameters
-REPRESENTATIVE = {1024: (2, 1, 64), 2048: (2, 1, 64), 4096: (2, 1, 64), 8192: (4, 1, 64), 16384: (8, 1, 32),
+# (at N = 16384 the batch is the genotype step's multiply tile: its squarings launch about 470 ciphertexts at a
+# time, in tiles of 128)
+REPRESENTATIVE = {1024: (2, 1, 64), 2048: (2, 1, 64), 4096: (2, 1, 64), 8192: (4, 1, 64), 16384: (8, 1, 128),
                   32768: (16, 2, 8)}
 TILES = (4, 8, 16, 32, 64, 128, 0)   # 0: as many as the scratch budget holds
 
@@ -66,7 +68,7 @@ def tune_ring(N, verbose=False):
         bfhe.ntt_config(logN, 0, fm, fe)
         for im, ie in shapes(logN):
             bfhe.ntt_config(logN, 1, im, ie)
-            timings["%d,%d/%d,%d" % (fm, fe, im, ie)] = _best_ms(torch, lambda: ctx.mul_relin(x, y, out=z))
+            timings["%d,%d/%d,%d" % (fm, fe, im, ie)] = _best_ms(torch, lambda: ctx.mul_relin(x, y, out=z), reps=5)
     best = min(timings, key=timings.get)
     fwd, inv = ([int(v) for v in part.split(",")] for part in best.split("/"))
     bfhe.ntt_config(logN, 0, *fwd)
