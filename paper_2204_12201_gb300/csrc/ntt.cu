@@ -32,9 +32,10 @@
 // cluster barrier after those reads keeps an in-place transform from
 // overwriting words the partner has not read yet.
 // Inverse: the two CTAs form a thread-block cluster; after the inner stages
-// each publishes its half in shared memory, reads the partner's through
-// distributed shared memory and finishes the outermost stage (and the twist)
-// for its own half.
+// the outermost stage pairs word j of the first half with word j of the
+// second: CTA 0 takes the pairs with j < M/2, CTA 1 the others, each reading
+// the partner's word of its pairs through distributed shared memory, making
+// the pair's one product and writing both outputs (and the twist).
 #include <cooperative_groups.h>
 
 #include <atomic>
@@ -253,27 +254,39 @@ __device__ __forceinline__ void inv_pass(u64 (&x)[1 << LOG_E], u64* sm, int tid,
         __syncthreads();
         inv_pass<LOG_M, LOG_E, P + 1, MODE, OUT>(x, sm, tid, itw, twist, q, in, out, half);
     } else if constexpr (MODE == 2) {
-        // outermost stage across the halves: publish, read the partner's words at the same
-        // block positions through distributed shared memory, finish, twist
+        // outermost stage across the halves, pairs (j, j + M): the top bit of e is bit LOG_M - 1 of j, so
+        // CTA 0 takes the pairs with j < M/2 and CTA 1 those with j >= M/2; each publishes the words of the
+        // other set, reads the partner's word of each pair it takes through distributed shared memory,
+        // makes the pair's one product and writes both outputs (the limb's positions j and j + M)
         cg::cluster_group cl = cg::this_cluster();
+        constexpr int EH = E / 2;
+        // (register indices stay compile-time: the half selects between two words)
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[pb + poff<W_LO>(e)] = x[e];
+        for (int e = 0; e < EH; ++e) {
+            const u64 v = half ? x[e] : x[e + EH];   // the set the partner takes
+            sm[pb + (half ? poff<W_LO>(e) : poff<W_LO>(e + EH))] = v;
+        }
         cl.sync();
         const u64* peer = cl.map_shared_rank(sm, cl.block_rank() ^ 1u);
         const u64 q4 = 4 * q;
+        u64* o = out - (size_t)half * M;        // limb start
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int j = base + (e << W_LO);
-            const u64 other = peer[pb + poff<W_LO>(e)];
-            const u64 U = half ? other : x[e], V = half ? x[e] : other;
+        for (int e = 0; e < EH; ++e) {
+            const u64 mine = half ? x[e + EH] : x[e];
+            const int off = half ? poff<W_LO>(e + EH) : poff<W_LO>(e);
+            const int j = base + ((half ? e + EH : e) << W_LO);
+            const u64 other = peer[pb + off];
+            const u64 U = half ? other : mine, V = half ? mine : other;
             const ulonglong2 wp = __ldg(itw + M + j);
             const u64 T = shoup_lazy4n(V, wp.x, wp.y, 0 - q);
-            const u64 y = half ? U + q4 - T : U + T;
+            const u64 y0 = U + T, y1 = U + q4 - T;
             if constexpr (OUT == 2) {
-                out[j] = y;
+                o[j] = y0;
+                o[j + M] = y1;
             } else {
-                const ulonglong2 tw = __ldg(twist + j + half * M);
-                out[j] = OUT == 1 ? shoup_lazy(y, tw.x, tw.y, q) : shoup(y, tw.x, tw.y, q);
+                const ulonglong2 t0 = __ldg(twist + j), t1 = __ldg(twist + j + M);
+                o[j] = OUT == 1 ? shoup_lazy(y0, t0.x, t0.y, q) : shoup(y0, t0.x, t0.y, q);
+                o[j + M] = OUT == 1 ? shoup_lazy(y1, t1.x, t1.y, q) : shoup(y1, t1.x, t1.y, q);
             }
         }
         cl.sync();   // the partner has finished reading this CTA's shared memory
