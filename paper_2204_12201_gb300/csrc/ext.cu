@@ -154,6 +154,32 @@ __device__ __forceinline__ u64 fast_eval(const uint32_t (&y0)[NS], const uint32_
     return sub_mod(redc(hi, lo, T, d.dst_qinv[j]), d.vS[(size_t)j * (NS + 1) + v], T);
 }
 
+// the same sum with three limb products per term (Karatsuba): the weight-2^26 part is
+// sum (y0 + y1)(c0 + c1) - sum y0 c0 - sum y1 c1, the same integer (every factor below 2^27, every product
+// below 2^54, so each sum fits 64 bits for fewer than 2^10 sources); scale-and-round takes this form, the base
+// extension of the multiply's inputs keeps four products (fewer registers)
+template <int NS, int ND>
+__device__ __forceinline__ u64 fast_eval3(const uint32_t (&y0)[NS], const uint32_t (&y1)[NS], int v, const ExtDesc& d,
+                                          const FastTab<NS, ND>& ft, int j) {
+    static_assert(NS < 1024, "the three-product sums are bounded for fewer than 2^10 sources");
+    u64 p00 = 0, pm = 0, p11 = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const uint32_t c0 = ft.c[j][i].x, c1 = ft.c[j][i].y;
+        p00 += (u64)y0[i] * c0;
+        p11 += (u64)y1[i] * c1;
+        pm += (u64)(y0[i] + y1[i]) * (c0 + c1);
+    }
+    const u64 mid = pm - p00 - p11;                  // weight 2^26
+    u64 lo = p00 + (mid << 26);
+    u64 hi = (mid >> 38) + (lo < p00 ? 1ull : 0ull);
+    const u64 top = p11 << 52;                       // weight 2^52
+    lo += top;
+    hi += (p11 >> 12) + (lo < top ? 1ull : 0ull);
+    const u64 T = d.dst_q[j];
+    return sub_mod(redc(hi, lo, T, d.dst_qinv[j]), d.vS[(size_t)j * (NS + 1) + v], T);
+}
+
 // X[c][slot] (slots a0 a1 b0 b1; only a0 a1 when squaring): Q limbs copied, B limbs = centred extension
 template <int NS, bool FAST>
 __global__ void __launch_bounds__(256, NS <= 8 ? 4 : 2) k_modup(const u64* A, const u64* B, u64* X, int n, int slots, int K, ExtDesc ext, int N,
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
                 const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], f.x, f.y, bj);   // [t d]_{b_j}, < 2 b_j
                 u64 rb;
                 if constexpr (FAST)
-                    rb = fast ? fast_eval<NS, KS>(r0, r1, vv, eQB, fq, j) : ext_eval<NS, false>(v, neg, eQB, j);
+                    rb = fast ? fast_eval3<NS, KS>(r0, r1, vv, eQB, fq, j) : ext_eval<NS, false>(v, neg, eQB, j);
                 else rb = ext_eval<NS, false>(v, neg, eQB, j);
                 y[j] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);  // (t d - r) / Q, < 2 b_j
             }
@@ -251,7 +277,7 @@ __global__ void __launch_bounds__(256, 2) k_scale(const u64* X, u64* C3, int n, 
             int vy = 0;
             if (fast_prep<KS, NS>(y, eBQ, fb, y0, y1, vy)) {
 #pragma unroll
-                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS, NS>(y0, y1, vy, eBQ, fb, i);
+                for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval3<KS, NS>(y0, y1, vy, eBQ, fb, i);
                 continue;
             }
         }
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(256, 2) k_scale_a(const u64* X, u64* Yt, int n
             const int pj = NS + (nP - 1 - NS - KS) + j;
             const ulonglong2 f = twist_at(twist, pj, 2, k, N);
             const u64 td = shoup_lazy(d[(size_t)(NS + j) * N], f.x, f.y, bj);
-            const u64 rb = fast_eval<NS, KS>(r0, r1, vv, eQB, fq, j);
+            const u64 rb = fast_eval3<NS, KS>(r0, r1, vv, eQB, fq, j);
             yo[(size_t)j * N] = shoup_lazy(td + bj - rb, Qinv_b[j], Qinv_b[KS + j], bj);
         }
     }
@@ -339,7 +365,7 @@ __global__ void __launch_bounds__(256, 2) k_scale_b(const u64* Yt, u64* C3, int 
         int vy = 0;
         if (fast_prep<KS, NS>(y, eBQ, fb, y0, y1, vy)) {
 #pragma unroll
-            for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval<KS, NS>(y0, y1, vy, eBQ, fb, i);
+            for (int i = 0; i < NS; ++i) o[(size_t)i * N] = fast_eval3<KS, NS>(y0, y1, vy, eBQ, fb, i);
             continue;
         }
         u64 w[KS];
