@@ -93,3 +93,29 @@ def test_library_parameter_rule_matches_the_oracle():
         prm = Params(N=N, L=L, alpha=alpha, t=t, prime_bits=bits)
         assert primes == prm.q + prm.p + prm.b, (N, L, alpha, t, bits)
         assert K == prm.K == L + 1
+
+
+def test_autotuner_search_space_is_what_the_library_accepts():
+    """Every NTT shape the autotuner tries is accepted by bfhe_ntt_config (host only), shapes outside it are
+    rejected, and the current configuration is restored afterwards."""
+    import pytest
+    lib, bfhe = _lib()
+    from paper_2204_12201_gb300 import autotune
+    for logN in range(10, 16):
+        saved = [bfhe.ntt_config(logN, inv) for inv in (0, 1)]
+        try:
+            tried = set(autotune.shapes(logN))
+            assert tried, logN
+            for m, e in tried:
+                for inv in (0, 1):
+                    assert bfhe.ntt_config(logN, inv, m, e) == (m, e)
+            for m in range(8, 17):
+                for e in range(2, 7):
+                    if (m, e) in tried:
+                        continue
+                    with pytest.raises(bfhe.BfheError):
+                        bfhe.ntt_config(logN, 0, m, e)
+        finally:
+            for inv, (m, e) in enumerate(saved):
+                bfhe.ntt_config(logN, inv, m, e)
+        assert [bfhe.ntt_config(logN, inv) for inv in (0, 1)] == saved
